@@ -1,0 +1,220 @@
+"""FP64 CPU oracle for the high-order thread-safe lattice Boltzmann step.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product library
+(``paper_2401_17074_b300``) never imports this package, and this package
+shares no code with it.
+
+The numerics live in ``tslb_oracle.cpp`` (population-based, direct
+per-direction sums of Eq. eqts / Eq. noneqts / Eq. pushLB of arXiv 2401.17074);
+this module only compiles it with g++/OpenMP and marshals numpy arrays.
+Array conventions match the C ABI: full-lattice arrays of N = nx*ny*nz nodes,
+x fastest; ``u`` is [3][N]; ``pi`` is [6][N] in the order xx, yy, zz, xy, xz, yz.
+"""
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tslb_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
+
+_lib = None
+
+
+def build(force=False):
+    """Compile the oracle shared library with g++ -O3 -fopenmp."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["g++", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c++17",
+                               "-o", _LIB, _SRC])
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        ip = ctypes.POINTER(ctypes.c_int)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        L.orc_lattice.argtypes = [ip, dp]
+        L.orc_feq3.argtypes = [ctypes.c_double, dp, dp]
+        L.orc_fneq3.argtypes = [dp, dp, dp]
+        L.orc_post.argtypes = [ctypes.c_double, dp, dp, ctypes.c_double, dp, dp]
+        L.orc_moments.argtypes = [dp, dp, dp, dp]
+        L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.orc_inflow_noise.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        L.orc_inflow_noise.restype = ctypes.c_double
+        L.orc_create.argtypes = [i64p, ctypes.c_double, dp, ip, i64p, dp, ctypes.c_uint64, ip]
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_init_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
+        L.orc_set_force_field.argtypes = [ctypes.c_void_p, dp]
+        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        L.orc_get_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
+        L.orc_get_populations.argtypes = [ctypes.c_void_p, dp]
+        L.orc_time.argtypes = [ctypes.c_void_p]
+        L.orc_time.restype = ctypes.c_int64
+        L.orc_complex_run.argtypes = [i64p, ctypes.c_double, ip, dp, dp, dp, dp, dp, ctypes.c_int64, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def lattice():
+    """Return (c [27,3] int, w [27]) in the oracle's direction order."""
+    c = np.zeros((27, 3), dtype=np.int32)
+    w = np.zeros(27)
+    lib().orc_lattice(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(w))
+    return c, w
+
+
+def feq3(rho, u):
+    out = np.zeros(27)
+    u = _f64(u)
+    lib().orc_feq3(float(rho), _d(u), _d(out))
+    return out
+
+
+def fneq3(pi6, u):
+    out = np.zeros(27)
+    pi6, u = _f64(pi6), _f64(u)
+    lib().orc_fneq3(_d(pi6), _d(u), _d(out))
+    return out
+
+
+def post_collision(rho, u, pi6, omega, F=(0.0, 0.0, 0.0)):
+    out = np.zeros(27)
+    u, pi6, F = _f64(u), _f64(pi6), _f64(F)
+    lib().orc_post(float(rho), _d(u), _d(pi6), float(omega), _d(F), _d(out))
+    return out
+
+
+def moments(f):
+    f = _f64(f)
+    rho = np.zeros(1)
+    u = np.zeros(3)
+    pi6 = np.zeros(6)
+    lib().orc_moments(_d(f), _d(rho), _d(u), _d(pi6))
+    return rho[0], u, pi6
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    p = ctypes.POINTER(ctypes.c_uint32)
+    lib().orc_philox4x32_10(c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
+    return out
+
+
+def inflow_noise(seed, x, y, t):
+    return lib().orc_inflow_noise(int(seed), int(x), int(y), int(t))
+
+
+class OracleSim:
+    """Population-based FP64 TSLB simulation on a full nx*ny*nz lattice.
+
+    bc = (x-, x+, y-, y+, z-, z+) face codes.  A non-periodic face makes the
+    outermost node layer a boundary layer (solid for BOUNCEBACK / FREESLIP,
+    ghost for INFLOW / OUTFLOW); only interior nodes are updated.
+    inflow = dict(center2=(cx2, cy2), diameter=D, u_jet=U, noise_amp=a, seed=s).
+    """
+
+    def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, inflow=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        d = np.array(self.dims, dtype=np.int64)
+        F = _f64(force)
+        b = np.array(bc, dtype=np.int32)
+        ii = np.zeros(3, dtype=np.int64)
+        dd = np.zeros(2)
+        seed = 0
+        if inflow is not None:
+            ii[:] = [inflow["center2"][0], inflow["center2"][1], inflow["diameter"]]
+            dd[:] = [inflow["u_jet"], inflow["noise_amp"]]
+            seed = int(inflow["seed"])
+        st = ctypes.c_int(0)
+        self._h = lib().orc_create(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(tau), _d(F),
+                                   b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                   ii.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _d(dd),
+                                   seed, ctypes.byref(st))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration (status %d)" % st.value)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def init_moments(self, rho, u, pi=None):
+        rho = _f64(rho).reshape(-1)
+        u = _f64(u).reshape(-1)
+        pi_p = None
+        if pi is not None:
+            pi = _f64(pi).reshape(-1)
+            pi_p = _d(pi)
+        assert rho.size == self.N and u.size == 3 * self.N
+        lib().orc_init_moments(self._h, _d(rho), _d(u), pi_p)
+
+    def set_force_field(self, F):
+        if F is None:
+            lib().orc_set_force_field(self._h, None)
+            return
+        F = _f64(F).reshape(-1)
+        assert F.size == 3 * self.N
+        lib().orc_set_force_field(self._h, _d(F))
+
+    def step(self, n=1):
+        st = lib().orc_step(self._h, int(n))
+        if st != 0:
+            raise RuntimeError("oracle step failed (%d)" % st)
+
+    @property
+    def t(self):
+        return lib().orc_time(self._h)
+
+    def get_moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros(3 * self.N)
+        pi = np.zeros(6 * self.N)
+        lib().orc_get_moments(self._h, _d(rho), _d(u), _d(pi))
+        return rho, u.reshape(3, self.N), pi.reshape(6, self.N)
+
+    def get_populations(self):
+        f = np.zeros(27 * self.N)
+        lib().orc_get_populations(self._h, _d(f))
+        return f.reshape(self.N, 27)
+
+
+def complex_step_energy(dims, tau, bc, rho, u, pi, F_re, F_im, nsteps):
+    """J = 1/2 sum rho u.u after nsteps, with a complex force field (F_re + i F_im).
+
+    Returns the complex J as a Python complex; Im(J)/h for F_im = h v is the
+    directional derivative of J along v (complex-step differentiation).
+    """
+    d = np.array(dims, dtype=np.int64)
+    b = np.array(bc, dtype=np.int32)
+    rho, u = _f64(rho).reshape(-1), _f64(u).reshape(-1)
+    pi = _f64(pi).reshape(-1) if pi is not None else np.zeros(6 * rho.size)
+    F_re, F_im = _f64(F_re).reshape(-1), _f64(F_im).reshape(-1)
+    jr = ctypes.c_double(0.0)
+    ji = ctypes.c_double(0.0)
+    st = lib().orc_complex_run(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(tau),
+                               b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(rho), _d(u), _d(pi),
+                               _d(F_re), _d(F_im), int(nsteps), ctypes.byref(jr), ctypes.byref(ji))
+    if st != 0:
+        raise ValueError("oracle rejected the configuration (status %d)" % st)
+    return complex(jr.value, ji.value)
