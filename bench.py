@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the D3Q27 high-order thread-safe LB step (arXiv 2401.17074) on one B300.
+
+Workload: the turbulent channel, 512 x 130 x 256 lattice with halfway
+bounce-back walls on the y = 0 and y = 129 layers, periodic in x and z,
+tau = 0.503, constant body force g = u_tau^2 / H (u_tau = 0.0035, H = 64),
+seeded laminar parabola + 2 % noise (synthetic; the paper's channel runs are
+the model).  A "step" is one TSLB step over all 512*128*256 interior nodes.
+
+Prints ONE JSON line (rank 0): MLUPS with inputs resident in HBM, the HBM
+roofline of the step kernel, the 16-bit storage variants, an end-to-end
+figure through the C ABI with host buffers, the FP64 oracle timed on the
+host cores, and the SM clocks sampled during the timed region.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has: the paper ships no code) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline (D3Q27 TSLB step, 1 B300), FP32 vs BF16 storage"
+BYTES_PER_NODE = {"fp32": 80, "bf16": 40, "fp16": 40}
+PREC_CODE = {"fp32": 0, "bf16": 1, "fp16": 2}
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="tslb", choices=["tslb", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "factored"])
+    ap.add_argument("--nx", type=int, default=512)
+    ap.add_argument("--ny", type=int, default=130)
+    ap.add_argument("--nz", type=int, default=256)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_record(kernel_name, precision):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel source is unchanged since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        recs = json.load(f)
+    for r in recs:
+        if r.get("kernel") != kernel_name or r.get("precision") != precision:
+            continue
+        src = os.path.join(ROOT, r["source"])
+        if not os.path.exists(src):
+            return None
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if h != r.get("source_sha256"):
+            return None
+        return float(r["bytes_per_launch_full"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_state(nx, ny, nz):
+    from paper_2401_17074_b300 import workloads as W
+    prm = W.channel_params(nx=nx, ny=ny, nz=nz)
+    state = W.channel_state(prm, seed=1)
+    return prm, state
+
+
+def cpu_baseline(prm, seconds, nz_sample=None):
+    """Time the FP64 oracle as it stands on a slab of the channel (periodic z) on all host cores."""
+    import oracle
+    from paper_2401_17074_b300 import workloads as W
+    nx, ny, _ = prm["dims"]
+    nz_s = nz_sample or 8
+    sub = W.channel_params(nx=nx, ny=ny, nz=nz_s)
+    state = W.channel_state(sub, seed=1)
+    s = oracle.OracleSim(sub["dims"], sub["tau"], force=sub["force"], bc=sub["bc"])
+    s.init_moments(*state)
+    nodes = nx * (ny - 2) * nz_s
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        s.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 1000:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": nodes * steps / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%dx%dx%d slab of the channel (periodic z), %d steps, FP64 populations, %.1f s"
+                      % (nx, ny, nz_s, steps, el)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2401_17074_b300 import workloads as W
+    nx, ny = args.nx, args.ny
+    # Calibrate: one oracle step on a 3-layer slab, then size the per-step sample so
+    # the whole warm-up + timed run stays within about two minutes.
+    budget = 120.0
+    nzs = 3
+    probe = W.channel_params(nx=nx, ny=ny, nz=nzs)
+    s = oracle.OracleSim(probe["dims"], probe["tau"], force=probe["force"], bc=probe["bc"])
+    s.init_moments(*W.channel_state(probe, seed=1))
+    t0 = time.perf_counter()
+    s.step(1)
+    rate = nx * (ny - 2) * nzs / (time.perf_counter() - t0)  # node updates / s
+    per_step = budget / max(1, args.steps + args.warmup)
+    sx = int(max(3, min(nx, per_step * rate / ((ny - 2) * nzs))))
+    sub = W.channel_params(nx=sx, ny=ny, nz=nzs)
+    s = oracle.OracleSim(sub["dims"], sub["tau"], force=sub["force"], bc=sub["bc"])
+    s.init_moments(*W.channel_state(sub, seed=1))
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    el = time.perf_counter() - t0
+    nodes = sx * (ny - 2) * nzs
+    v = nodes * args.steps / el / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "%dx%dx%d sub-box of the channel (periodic x, z), FP64 populations, %d steps" % (sx, ny, nzs, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "turbulent channel %dx%dx%d (bounded sample per step)" % (nx, ny, args.nz),
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, dist, clocks=None):
+    s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], precision=PREC_CODE[precision],
+                 kernel=kernel, stream=stream.cuda_stream, pi_ref=4e-4)
+    s.init_moments(*state)
+    s.step(warmup)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    if clocks:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ck = clocks.stop() if clocks else None
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    d, code = s.diagnostics()
+    nodes = s.interior_nodes()
+    s.close()
+    return ms, nodes, d, code, ck
+
+
+def time_e2e(T, torch, prm, state, steps, stream):
+    """End to end through the C ABI: pinned host FP64 moments in, K steps, moments back to pinned host."""
+    rho, u, pi = state
+    N = rho.size
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_u = torch.from_numpy(u.reshape(-1)).pin_memory()
+    h_pi = torch.from_numpy(pi.reshape(-1)).pin_memory()
+    o_rho = torch.empty(N, dtype=torch.float64).pin_memory()
+    o_u = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+    o_pi = torch.empty(6 * N, dtype=torch.float64).pin_memory()
+    s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], stream=stream.cuda_stream)
+    # one untimed pass to settle allocator pools
+    T.tslb_init_moments(s.handle, h_rho, h_u, h_pi)
+    s.step(2)
+    T.tslb_get_moments(s.handle, o_rho, o_u, o_pi, T.HOST)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T.tslb_init_moments(s.handle, h_rho, h_u, h_pi)
+    s.step(steps)
+    T.tslb_get_moments(s.handle, o_rho, o_u, o_pi, T.HOST)
+    el = time.perf_counter() - t0
+    nodes = s.interior_nodes()
+    s.close()
+    return {"value": nodes * steps / el / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": int(8 * 10 * N / steps), "d2h_bytes_per_step": int(8 * 10 * N / steps),
+            "note": "init from pinned host FP64 moments + %d steps + moments back to pinned host, wall clock" % steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    else:
+        torch.cuda.set_device(0)
+    import paper_2401_17074_b300 as T
+    T.load()
+    kernel = {"auto": T.KERNEL_AUTO, "direct": T.KERNEL_DIRECT, "factored": T.KERNEL_FACTORED}[args.kernel]
+    prm, state = make_state(args.nx, args.ny, args.nz)
+    stream = torch.cuda.Stream()
+    hbm, hbm_src = measured_peaks()
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    ms, nodes, diag, code, ck = time_device(T, torch, prm, state, args.precision, kernel, args.steps, args.warmup,
+                                            stream, dist, clocks)
+    total_nodes = nodes * ws
+    value = total_nodes * args.steps / (ms * 1e-3) / 1e6
+    launch_s = ms * 1e-3 / args.steps
+    bpn = BYTES_PER_NODE[args.precision]
+    achieved = bpn * nodes / launch_s / 1e9
+    from paper_2401_17074_b300 import build as B
+    kname = "tslb_step_factored" if kernel != T.KERNEL_DIRECT else "tslb_step_direct"
+    traffic = traffic_record(kname, args.precision)
+
+    variants = {}
+    if not args.no_variants:
+        for prec in ("bf16", "fp16"):
+            if prec == args.precision:
+                continue
+            msv, nv, dv, cv, _ = time_device(T, torch, prm, state, prec, kernel, args.steps, args.warmup, stream, dist)
+            ls = msv * 1e-3 / args.steps
+            variants[prec] = {"value": nv * ws * args.steps / (msv * 1e-3) / 1e6, "unit": "MLUPS",
+                              "roofline_frac": BYTES_PER_NODE[prec] * nv / ls / 1e9 / hbm,
+                              "bytes_per_node": BYTES_PER_NODE[prec], "stable": cv == T.TSLB_OK}
+        if args.precision != "fp32":
+            pass
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = time_e2e(T, torch, prm, state, args.steps, stream)
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        cpu = cpu_baseline(prm, args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded laminar parabola + 2% noise)",
+            "config": {"workload": "turbulent channel %dx%dx%d, bounce-back walls y=0,%d, periodic x,z, tau=0.503, "
+                                   "g=%.4g; %s moment storage" % (args.nx, args.ny, args.nz, args.ny - 1,
+                                                                  prm["force"][0], args.precision),
+                       "interior_nodes": nodes, "storage": args.precision,
+                       "l2": "inputs larger than L2: two %.0f MB moment buffers" % (bpn / 2 * nodes / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single GPU", "kernel": kname},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": traffic, "peak_source": hbm_src,
+                         "algorithmic_bytes_per_node": bpn, "kernel": kname},
+            "variants": variants,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "clocks": ck,
+            "diagnostics_after_timed": {"mass": diag["mass"], "max_speed": diag["max_speed"], "status": code},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * tslb.h -- C ABI of the B300 (sm_103a) high-order thread-safe lattice
+ * Boltzmann library (arXiv 2401.17074, "High-order thread-safe lattice
+ * Boltzmann model for HPC turbulent flow simulations").
+ *
+ * The library advances a D3Q27 lattice whose state is only the 10 macroscopic
+ * moment fields per node -- density rho, velocity u and the non-equilibrium
+ * momentum flux Pi^neq (Sec. 2.1, the "10 arrays" of the thread-safe scheme).
+ * One step rebuilds, at every node x, the post-collision populations of its
+ * 26 neighbours x - c_i from their moments by third-order recursive Hermite
+ * regularisation (Eq. eqts, Eq. noneqts, the combined update after
+ * Eq. noneqts), streams them (Eq. pushLB, written in pull form) and sums the
+ * new moments.  Body forcing (Luo term, Sec. 3.1) and wall / inflow / outflow
+ * faces (Sec. 2.3, Sec. 3.2) are applied in the same pass.
+ *
+ * Conventions shared by every call:
+ *   - Lattice coordinates (x, y, z) run over dims[0] x dims[1] x dims[2]
+ *     nodes, x fastest; node index n = x + nx*(y + ny*z); N = nx*ny*nz.
+ *   - A non-periodic face turns the outermost node layer on that side into a
+ *     boundary layer: solid for BOUNCEBACK / FREESLIP (walls halfway between
+ *     it and the first interior layer), a ghost layer for INFLOW / OUTFLOW.
+ *     Only interior nodes are stored and updated; "interior nodes" below is
+ *     the product of the interior extents.
+ *   - Moment arrays exchanged with the caller are full-lattice FP64 arrays:
+ *     rho[N]; u[3][N] (u_x, u_y, u_z planes); pi[6][N] in the order
+ *     xx, yy, zz, xy, xz, yz.  Boundary-layer entries are ignored on input
+ *     and returned as the rest state (rho = 1, u = 0, Pi = 0) on output.
+ *   - `where` says whether a pointer is host memory (TSLB_HOST, pageable or
+ *     pinned) or device memory on the handle's device (TSLB_DEVICE).
+ *   - Every call returns TSLB_OK (0) or a negative tslb_status; on error the
+ *     handle is unchanged unless stated and tslb_last_error() explains.  No
+ *     call aborts the process or traps the device.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef TSLB_H
+#define TSLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tslb_s tslb_t;
+
+typedef enum tslb_status {
+    TSLB_OK = 0,
+    TSLB_ERR_INVALID = -1,     /* bad argument (null pointer, tau <= 1/2, size too small, ...) */
+    TSLB_ERR_UNSUPPORTED = -2, /* valid request this library does not implement */
+    TSLB_ERR_CUDA = -3,        /* a CUDA runtime call failed; see tslb_last_error */
+    TSLB_ERR_ALLOC = -4,       /* device or host allocation failed */
+    TSLB_ERR_UNSTABLE = -5,    /* diagnostics found NaN/Inf in the moment fields */
+    TSLB_ERR_STATE = -6        /* call not valid in the handle's current state */
+} tslb_status;
+
+enum { TSLB_D3Q27 = 27 };
+
+/* Face boundary conditions, indexed bc[0..5] = x-, x+, y-, y+, z-, z+. */
+typedef enum tslb_bc {
+    TSLB_BC_PERIODIC = 0,   /* both faces of the axis must be periodic */
+    TSLB_BC_BOUNCEBACK = 1, /* halfway bounce-back no-slip wall (y faces only) */
+    TSLB_BC_FREESLIP = 2,   /* halfway specular-reflection wall (x or y faces) */
+    TSLB_BC_INFLOW = 3,     /* z- only: thread-safe Hermite non-equilibrium inflow, Eq. neq_final */
+    TSLB_BC_OUTFLOW = 4     /* z+ only: zero-gradient outflow (moments of the adjacent layer) */
+} tslb_bc;
+
+typedef enum tslb_precision {
+    TSLB_FP32 = 0, /* moments stored as FP32 (rho stored as rho - 1) */
+    TSLB_BF16 = 1, /* stored as BF16 scaled deviations: rho-1, u/u_ref, Pi/pi_ref */
+    TSLB_FP16 = 2  /* stored as FP16 scaled deviations */
+} tslb_precision;
+
+typedef enum tslb_where { TSLB_HOST = 0, TSLB_DEVICE = 1 } tslb_where;
+
+typedef enum tslb_kernel {
+    TSLB_KERNEL_AUTO = 0,     /* the fastest kernel that supports the configuration */
+    TSLB_KERNEL_DIRECT = 1,   /* one thread per node, 27 direct gathers (cross-check path) */
+    TSLB_KERNEL_FACTORED = 2  /* sum-factorised, z-marching tiled kernel */
+} tslb_kernel;
+
+/* Inflow nozzle of the round jet (Sec. 3.2): inside the disc
+ * (2x - center2[0])^2 + (2y - center2[1])^2 <= diameter^2 the imposed velocity
+ * is u_z = u_jet (1 + noise_amp * xi), xi uniform in [-1, 1) drawn per column
+ * and per step from Philox4x32-10 keyed by `seed`; outside it is zero. */
+typedef struct tslb_inflow {
+    int64_t center2[2];
+    int64_t diameter;
+    double u_jet;
+    double noise_amp;
+    uint64_t seed;
+} tslb_inflow;
+
+typedef struct tslb_options {
+    int precision;        /* tslb_precision, default TSLB_FP32 */
+    double u_ref;         /* velocity scale of 16-bit storage, default 0.05 */
+    double pi_ref;        /* Pi^neq scale of 16-bit storage, default 1e-3 */
+    void* stream;         /* cudaStream_t to run on; NULL = a stream owned by the handle */
+    int device;           /* CUDA device ordinal, default 0 */
+    int kernel;           /* tslb_kernel, default TSLB_KERNEL_AUTO */
+    int checkpoint_every; /* >0: tslb_step records a moment checkpoint every k steps (adjoint) */
+    tslb_inflow inflow;   /* used when bc[4] == TSLB_BC_INFLOW */
+} tslb_options;
+
+typedef struct tslb_diag {
+    double mass;           /* sum over interior nodes of rho */
+    double momentum[3];    /* sum of rho u */
+    double kinetic_energy; /* 1/2 sum rho |u|^2 */
+    double wall_shear;     /* y walls: mean of -(1-omega/2) Pi_xy on y=1 and +(...) on y=ny-2; else 0 */
+    double max_speed;      /* max |u| (Mach check) */
+    int64_t nonfinite;     /* number of interior nodes with a NaN/Inf moment */
+    int64_t steps;         /* steps taken since tslb_init_moments */
+    int64_t nodes;         /* interior nodes */
+} tslb_diag;
+
+/* Fill *opt with the defaults listed above.  Returns TSLB_ERR_INVALID if opt is NULL. */
+int tslb_options_default(tslb_options* opt);
+
+/* Create a solver (problem statement of Sec. 2 and Sec. 3: lattice, grid, tau
+ * with nu = cs^2 (tau - 1/2), constant body-force acceleration `force`
+ * (Sec. 3.1; NULL = 0), face conditions `bc`).  The library allocates and owns
+ * all device memory (two buffers of the 10 moment fields).  Rejects tau <= 1/2,
+ * an axis shorter than 3 (periodic) or 4 (otherwise), mixed periodic /
+ * non-periodic faces on one axis (TSLB_ERR_INVALID), and any lattice other than
+ * TSLB_D3Q27 or a face combination not listed in tslb_bc (TSLB_ERR_UNSUPPORTED).
+ * *out is written only on success.  The moment fields start at the rest state. */
+int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, const double force[3],
+                const int bc[6], const tslb_options* opt);
+
+/* Load the moment fields (Sec. 2.1: rho, u, Pi^neq) from full-lattice FP64
+ * arrays; `pi` may be NULL (Pi^neq = 0).  The caller keeps ownership; the call
+ * returns after the data are copied.  Resets the step counter to 0. */
+int tslb_init_moments(tslb_t* h, const double* rho, const double* u, const double* pi, int where);
+
+/* Per-node body-force acceleration F[3][N] (FP32, full lattice) replacing the
+ * constant force; NULL restores the constant force given to tslb_create. */
+int tslb_set_force_field(tslb_t* h, const float* F, int where);
+
+/* Advance nsteps TSLB steps (Eq. pushLB with Eq. eqts / Eq. noneqts
+ * reconstruction, forcing and faces), asynchronously on the handle's stream.
+ * Launch errors are reported immediately; the call does not synchronise. */
+int tslb_step(tslb_t* h, int64_t nsteps);
+
+/* Copy the current moments out as full-lattice FP64 arrays (any pointer may
+ * be NULL to skip that field).  Synchronises the handle's stream. */
+int tslb_get_moments(tslb_t* h, double* rho, double* u, double* pi, int where);
+
+/* FP64 reductions over the interior nodes (mass, momentum, kinetic energy,
+ * wall shear, max |u|, NaN/Inf count).  Synchronises the stream.  Returns
+ * TSLB_ERR_UNSTABLE (with *out filled) if any moment is NaN or Inf. */
+int tslb_diagnostics(tslb_t* h, tslb_diag* out);
+
+/* Gradient of J = 1/2 sum rho |u|^2 at the current step with respect to a
+ * time-constant per-node body-force field, back-propagated through the last
+ * `nsteps` steps taken since tslb_init_moments by the discrete adjoint of the
+ * step.  Requires options.checkpoint_every > 0 at create time; segments
+ * between checkpoints are recomputed.  dJdF is a full-lattice FP32 [3][N]
+ * array (boundary entries 0).  Synchronises the stream. */
+int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where);
+
+/* Number of interior (updated) nodes. */
+int64_t tslb_interior_nodes(const tslb_t* h);
+
+/* Block until all work queued on the handle's stream is done. */
+int tslb_synchronize(tslb_t* h);
+
+/* Release all memory of the handle.  NULL is ignored. */
+void tslb_destroy(tslb_t* h);
+
+/* Text of the last error on this handle (never NULL).  For h == NULL, the
+ * last error of a failed tslb_create on this thread. */
+const char* tslb_last_error(const tslb_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSLB_H */

@@ -1,0 +1,279 @@
+"""Python binding of the B300 high-order thread-safe lattice Boltzmann library.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``libtslb.so`` (built from ``csrc/`` by ``build.py``).  The functions keep
+the C names of ``include/tslb.h``; ``Solver`` is a small convenience wrapper
+that accepts numpy arrays or CUDA torch tensors.  Loading fails loudly when
+the shared library is missing -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TSLB_OK = 0
+TSLB_ERR_INVALID = -1
+TSLB_ERR_UNSUPPORTED = -2
+TSLB_ERR_CUDA = -3
+TSLB_ERR_ALLOC = -4
+TSLB_ERR_UNSTABLE = -5
+TSLB_ERR_STATE = -6
+
+TSLB_D3Q27 = 27
+PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
+FP32, BF16, FP16 = 0, 1, 2
+HOST, DEVICE = 0, 1
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED = 0, 1, 2
+
+EXPORTED = [
+    "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_set_force_field", "tslb_step",
+    "tslb_get_moments", "tslb_diagnostics", "tslb_adjoint_force_gradient", "tslb_interior_nodes",
+    "tslb_synchronize", "tslb_destroy", "tslb_last_error",
+]
+
+
+class tslb_inflow(ctypes.Structure):
+    _fields_ = [("center2", ctypes.c_int64 * 2), ("diameter", ctypes.c_int64), ("u_jet", ctypes.c_double),
+                ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class tslb_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("u_ref", ctypes.c_double), ("pi_ref", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("checkpoint_every", ctypes.c_int), ("inflow", tslb_inflow)]
+
+
+class tslb_diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("kinetic_energy", ctypes.c_double),
+                ("wall_shear", ctypes.c_double), ("max_speed", ctypes.c_double), ("nonfinite", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("nodes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {"mass": self.mass, "momentum": list(self.momentum), "kinetic_energy": self.kinetic_energy,
+                "wall_shear": self.wall_shear, "max_speed": self.max_speed, "nonfinite": self.nonfinite,
+                "steps": self.steps, "nodes": self.nodes}
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libtslb.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libtslb.so is missing; run paper_2401_17074_b300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, dp, fp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+    L.tslb_options_default.argtypes = [ctypes.POINTER(tslb_options)]
+    L.tslb_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(i64), ctypes.c_double, dp,
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(tslb_options)]
+    L.tslb_init_moments.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    L.tslb_set_force_field.argtypes = [vp, fp, ctypes.c_int]
+    L.tslb_step.argtypes = [vp, i64]
+    L.tslb_get_moments.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    L.tslb_diagnostics.argtypes = [vp, ctypes.POINTER(tslb_diag)]
+    L.tslb_adjoint_force_gradient.argtypes = [vp, i64, fp, ctypes.c_int]
+    L.tslb_interior_nodes.argtypes = [vp]
+    L.tslb_interior_nodes.restype = i64
+    L.tslb_synchronize.argtypes = [vp]
+    L.tslb_destroy.argtypes = [vp]
+    L.tslb_destroy.restype = None
+    L.tslb_last_error.argtypes = [vp]
+    L.tslb_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+class TslbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("tslb error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(code, h=None):
+    if code != TSLB_OK:
+        msg = load().tslb_last_error(h).decode(errors="replace")
+        raise TslbError(code, msg)
+    return code
+
+
+# ---- C-named thin wrappers --------------------------------------------------
+
+def tslb_options_default():
+    o = tslb_options()
+    _check(load().tslb_options_default(ctypes.byref(o)))
+    return o
+
+
+def tslb_create(dims, tau, force=None, bc=(0,) * 6, opt=None, lattice=TSLB_D3Q27):
+    L = load()
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * 3)(*[int(v) for v in dims])
+    b = (ctypes.c_int * 6)(*[int(v) for v in bc])
+    f = (ctypes.c_double * 3)(*[float(v) for v in force]) if force is not None else None
+    code = L.tslb_create(ctypes.byref(h), int(lattice), d, float(tau), f, b,
+                         ctypes.byref(opt) if opt is not None else None)
+    _check(code, None)
+    return h
+
+
+def _ptr(a, dtype):
+    """Return (pointer, where, keepalive) for a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, HOST, None
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.float32
+        t = a.contiguous()
+        if t.dtype != want:
+            raise TypeError("expected %s tensor" % want)
+        return ctypes.c_void_p(t.data_ptr()), DEVICE, t
+    if hasattr(a, "numpy"):  # CPU torch tensor (pinned or pageable)
+        t = a.contiguous()
+        return ctypes.c_void_p(t.data_ptr()), HOST, t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), HOST, arr
+
+
+def tslb_init_moments(h, rho, u, pi=None):
+    pr, w, k1 = _ptr(rho, np.float64)
+    pu, w2, k2 = _ptr(u, np.float64)
+    pp, w3, k3 = _ptr(pi, np.float64)
+    if pi is not None and not (w == w2 == w3):
+        raise ValueError("rho, u, pi must all be host or all device")
+    _check(load().tslb_init_moments(h, pr, pu, pp, w), h)
+
+
+def tslb_set_force_field(h, F):
+    if F is None:
+        _check(load().tslb_set_force_field(h, None, HOST), h)
+        return
+    p, w, k = _ptr(F, np.float32)
+    _check(load().tslb_set_force_field(h, p, w), h)
+
+
+def tslb_step(h, nsteps=1):
+    _check(load().tslb_step(h, int(nsteps)), h)
+
+
+def tslb_get_moments(h, rho=None, u=None, pi=None, where=HOST):
+    def p(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return ctypes.c_void_p(a.data_ptr())
+        return ctypes.c_void_p(a.ctypes.data)
+    _check(load().tslb_get_moments(h, p(rho), p(u), p(pi), int(where)), h)
+
+
+def tslb_diagnostics(h):
+    d = tslb_diag()
+    code = load().tslb_diagnostics(h, ctypes.byref(d))
+    if code not in (TSLB_OK, TSLB_ERR_UNSTABLE):
+        _check(code, h)
+    return d, code
+
+
+def tslb_adjoint_force_gradient(h, nsteps, dJdF, where=HOST):
+    p = ctypes.c_void_p(dJdF.data_ptr() if hasattr(dJdF, "data_ptr") else dJdF.ctypes.data)
+    _check(load().tslb_adjoint_force_gradient(h, int(nsteps), p, int(where)), h)
+
+
+def tslb_interior_nodes(h):
+    return load().tslb_interior_nodes(h)
+
+
+def tslb_synchronize(h):
+    _check(load().tslb_synchronize(h), h)
+
+
+def tslb_destroy(h):
+    load().tslb_destroy(h)
+
+
+def tslb_last_error(h=None):
+    return load().tslb_last_error(h).decode(errors="replace")
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+class Solver:
+    """Owns one TSLB handle.  Arrays follow the C ABI layouts (full lattice, x fastest)."""
+
+    def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05, pi_ref=1e-3,
+                 kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None):
+        o = tslb_options_default()
+        o.precision = int(precision)
+        o.u_ref = float(u_ref)
+        o.pi_ref = float(pi_ref)
+        o.kernel = int(kernel)
+        o.device = int(device)
+        o.checkpoint_every = int(checkpoint_every)
+        if stream is not None:
+            o.stream = ctypes.c_void_p(int(stream))
+        if inflow is not None:
+            o.inflow.center2[0] = int(inflow["center2"][0])
+            o.inflow.center2[1] = int(inflow["center2"][1])
+            o.inflow.diameter = int(inflow["diameter"])
+            o.inflow.u_jet = float(inflow["u_jet"])
+            o.inflow.noise_amp = float(inflow["noise_amp"])
+            o.inflow.seed = int(inflow["seed"])
+        self.dims = tuple(int(d) for d in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self._h = tslb_create(self.dims, tau, force, bc, o)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            tslb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_moments(self, rho, u, pi=None):
+        tslb_init_moments(self._h, rho, u, pi)
+
+    def set_force_field(self, F):
+        tslb_set_force_field(self._h, F)
+
+    def step(self, n=1):
+        tslb_step(self._h, n)
+
+    def get_moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros(3 * self.N)
+        pi = np.zeros(6 * self.N)
+        tslb_get_moments(self._h, rho, u, pi, HOST)
+        return rho, u.reshape(3, self.N), pi.reshape(6, self.N)
+
+    def diagnostics(self):
+        d, code = tslb_diagnostics(self._h)
+        return d.as_dict(), code
+
+    def interior_nodes(self):
+        return tslb_interior_nodes(self._h)
+
+    def synchronize(self):
+        tslb_synchronize(self._h)
+
+    def adjoint_force_gradient(self, nsteps):
+        g = np.zeros(3 * self.N, dtype=np.float32)
+        tslb_adjoint_force_gradient(self._h, nsteps, g, HOST)
+        return g.reshape(3, self.N)

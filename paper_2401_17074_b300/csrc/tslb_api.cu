@@ -1,0 +1,425 @@
+// C ABI of the TSLB library (declared in include/tslb.h): argument checks,
+// device memory ownership, stream handling and kernel dispatch.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "tslb_internal.cuh"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(tslb_s* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(tslb_s* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, TSLB_ERR_CUDA, m);
+}
+
+// Host-side fault injection for the error-path tests: TSLB_FAULT=alloc makes
+// every device allocation of the library report failure without calling CUDA.
+bool inject_alloc_fault() {
+    const char* f = std::getenv("TSLB_FAULT");
+    return f && std::strcmp(f, "alloc") == 0;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t s) {
+    if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, s);
+}
+
+bool valid_handle(const tslb_s* h) { return h != nullptr; }
+
+void release(tslb_s* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b)
+        if (h->buf[b]) cudaFree(h->buf[b]);
+    if (h->force_field) cudaFree(h->force_field);
+    if (h->diag_part) cudaFree(h->diag_part);
+    if (h->diag_host) cudaFreeHost(h->diag_host);
+    for (void* c : h->ckpts) cudaFree(c);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // namespace
+
+namespace tslb {
+
+Physics make_physics(const tslb_s* h) {
+    Physics p{};
+    p.omega1 = (float)(1.0 - h->omega);
+    for (int a = 0; a < 3; ++a) p.F[a] = (float)h->force[a];
+    p.force = h->force_field;
+    p.in_c2[0] = h->inflow.center2[0];
+    p.in_c2[1] = h->inflow.center2[1];
+    p.in_d = h->inflow.diameter;
+    p.in_u = (float)h->inflow.u_jet;
+    p.in_amp = (float)h->inflow.noise_amp;
+    p.in_seed = h->inflow.seed;
+    p.t = h->t;
+    if (h->precision == TSLB_FP32) {
+        p.s_u = p.s_pi = p.inv_s_u = p.inv_s_pi = 1.0f;
+    } else {
+        p.s_u = (float)h->u_ref;
+        p.s_pi = (float)h->pi_ref;
+        p.inv_s_u = (float)(1.0 / h->u_ref);
+        p.inv_s_pi = (float)(1.0 / h->pi_ref);
+    }
+    return p;
+}
+
+bool use_factored(const tslb_s* h) { return h->kernel != TSLB_KERNEL_DIRECT && factored_supports(h); }
+
+cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p) {
+    return use_factored(h) ? launch_step_factored(h, src, dst, p) : launch_step_direct(h, src, dst, p);
+}
+
+}  // namespace tslb
+
+namespace {
+
+size_t state_bytes(const tslb_s* h) { return (size_t)tslb::NFIELDS * h->g.fstride * h->elem; }
+
+void drop_checkpoints(tslb_s* h) {
+    if (!h->ckpts.empty()) cudaStreamSynchronize(h->stream);
+    for (void* c : h->ckpts) cudaFree(c);
+    h->ckpts.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int tslb_options_default(tslb_options* opt) {
+    if (!opt) return TSLB_ERR_INVALID;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = TSLB_FP32;
+    opt->u_ref = 0.05;
+    opt->pi_ref = 1e-3;
+    opt->stream = nullptr;
+    opt->device = 0;
+    opt->kernel = TSLB_KERNEL_AUTO;
+    opt->checkpoint_every = 0;
+    return TSLB_OK;
+}
+
+int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, const double force[3],
+                const int bc[6], const tslb_options* opt) {
+    g_create_error.clear();
+    if (!out || !dims || !bc) return fail(nullptr, TSLB_ERR_INVALID, "null argument");
+    if (lattice != TSLB_D3Q27) return fail(nullptr, TSLB_ERR_UNSUPPORTED, "only TSLB_D3Q27 is implemented");
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, TSLB_ERR_INVALID, "tau must be > 1/2");
+    for (int f = 0; f < 6; ++f)
+        if (bc[f] < TSLB_BC_PERIODIC || bc[f] > TSLB_BC_OUTFLOW)
+            return fail(nullptr, TSLB_ERR_INVALID, "unknown boundary code");
+    for (int a = 0; a < 3; ++a) {
+        const bool p0 = bc[2 * a] == TSLB_BC_PERIODIC, p1 = bc[2 * a + 1] == TSLB_BC_PERIODIC;
+        if (p0 != p1) return fail(nullptr, TSLB_ERR_INVALID, "an axis mixes periodic and non-periodic faces");
+        if (dims[a] < (p0 ? 3 : 4)) return fail(nullptr, TSLB_ERR_INVALID, "axis too short");
+        if (dims[a] > (int64_t)1 << 30) return fail(nullptr, TSLB_ERR_INVALID, "axis too long");
+    }
+    // Supported face combinations (see tslb_bc).
+    const int bx = bc[0], by = bc[2], bz0 = bc[4], bz1 = bc[5];
+    if (bc[0] != bc[1] || bc[2] != bc[3])
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "x and y faces must match pairwise");
+    if (!(bx == TSLB_BC_PERIODIC || bx == TSLB_BC_FREESLIP))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "x faces: periodic or free-slip");
+    if (!(by == TSLB_BC_PERIODIC || by == TSLB_BC_FREESLIP || by == TSLB_BC_BOUNCEBACK))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "y faces: periodic, bounce-back or free-slip");
+    if (!((bz0 == TSLB_BC_PERIODIC && bz1 == TSLB_BC_PERIODIC) || (bz0 == TSLB_BC_INFLOW && bz1 == TSLB_BC_OUTFLOW)))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "z faces: periodic, or inflow (z-) with outflow (z+)");
+    if (by == TSLB_BC_BOUNCEBACK && (bx != TSLB_BC_PERIODIC || bz0 != TSLB_BC_PERIODIC))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "bounce-back y walls need periodic x and z");
+
+    tslb_options o;
+    if (opt) o = *opt;
+    else tslb_options_default(&o);
+    if (o.precision < TSLB_FP32 || o.precision > TSLB_FP16)
+        return fail(nullptr, TSLB_ERR_INVALID, "unknown precision");
+    if (o.precision != TSLB_FP32 && (!(o.u_ref > 0) || !(o.pi_ref > 0)))
+        return fail(nullptr, TSLB_ERR_INVALID, "16-bit storage needs positive u_ref and pi_ref");
+    if (o.kernel < TSLB_KERNEL_AUTO || o.kernel > TSLB_KERNEL_FACTORED)
+        return fail(nullptr, TSLB_ERR_INVALID, "unknown kernel choice");
+    if (o.checkpoint_every < 0) return fail(nullptr, TSLB_ERR_INVALID, "checkpoint_every < 0");
+    if (bz0 == TSLB_BC_INFLOW && o.inflow.diameter < 0) return fail(nullptr, TSLB_ERR_INVALID, "bad inflow diameter");
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
+    if (o.device < 0 || o.device >= ndev) return fail(nullptr, TSLB_ERR_INVALID, "bad device ordinal");
+
+    tslb_s* h = new tslb_s();
+    h->device = o.device;
+    for (int a = 0; a < 3; ++a) h->dims[a] = dims[a];
+    for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
+    h->tau = tau;
+    h->omega = 1.0 / tau;
+    for (int a = 0; a < 3; ++a) h->force[a] = force ? force[a] : 0.0;
+    h->precision = o.precision;
+    h->u_ref = o.u_ref;
+    h->pi_ref = o.pi_ref;
+    h->kernel = o.kernel;
+    h->checkpoint_every = o.checkpoint_every;
+    h->inflow = o.inflow;
+    h->elem = o.precision == TSLB_FP32 ? 4 : 2;
+
+    tslb::Geometry& g = h->g;
+    int ext[3];
+    for (int a = 0; a < 3; ++a) {
+        const bool per = bc[2 * a] == TSLB_BC_PERIODIC;
+        g.lo[a] = per ? 0 : 1;
+        ext[a] = (int)(per ? dims[a] : dims[a] - 2);
+    }
+    g.nx = ext[0];
+    g.ny = ext[1];
+    g.nz = ext[2];
+    for (int f = 0; f < 6; ++f) g.bc[f] = bc[f];
+    g.plane = (long long)g.nx * g.ny;
+    const long long Ni = g.plane * g.nz;
+    g.fstride = (Ni + 127) / 128 * 128;  // 512-byte aligned field planes (FP32)
+
+    e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(nullptr, e, "cudaSetDevice");
+        delete h;
+        return r;
+    }
+    if (o.stream) {
+        h->stream = (cudaStream_t)o.stream;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            int r = cuda_fail(nullptr, e, "cudaStreamCreate");
+            delete h;
+            return r;
+        }
+        h->own_stream = true;
+    }
+    const size_t bytes = (size_t)tslb::NFIELDS * g.fstride * h->elem;
+    for (int b = 0; b < 2; ++b) {
+        e = dev_alloc(&h->buf[b], bytes);
+        if (e != cudaSuccess) {
+            std::string m = std::string("device allocation of the moment fields failed: ") + cudaGetErrorString(e);
+            release(h);
+            return fail(nullptr, TSLB_ERR_ALLOC, m);
+        }
+        e = cudaMemsetAsync(h->buf[b], 0, bytes, h->stream);  // zero deviations = rest state
+        if (e != cudaSuccess) {
+            release(h);
+            return cuda_fail(nullptr, e, "cudaMemsetAsync");
+        }
+    }
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->diag_blocks = sms * 4;
+    e = dev_alloc((void**)&h->diag_part, sizeof(double) * 8 * (h->diag_blocks + 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&h->diag_host, sizeof(double) * 8);
+    if (e != cudaSuccess) {
+        std::string m = std::string("device allocation of the diagnostics scratch failed: ") + cudaGetErrorString(e);
+        release(h);
+        return fail(nullptr, TSLB_ERR_ALLOC, m);
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        release(h);
+        return cuda_fail(nullptr, e, "cudaStreamSynchronize");
+    }
+    *out = h;
+    return TSLB_OK;
+}
+
+int tslb_init_moments(tslb_t* h, const double* rho, const double* u, const double* pi, int where) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (!rho || !u) return fail(h, TSLB_ERR_INVALID, "rho and u are required");
+    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    cudaSetDevice(h->device);
+    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
+    const tslb::Physics p = tslb::make_physics(h);
+    cudaError_t e;
+    if (where == TSLB_DEVICE) {
+        e = tslb::launch_encode(h, rho, u, pi, h->buf[h->cur], p);
+        if (e != cudaSuccess) return cuda_fail(h, e, "encode launch");
+    } else {
+        double* st = nullptr;
+        const size_t bytes = sizeof(double) * (size_t)fN * (pi ? 10 : 4);
+        e = dev_alloc_async((void**)&st, bytes, h->stream);
+        if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "staging allocation failed");
+        e = cudaMemcpyAsync(st, rho, sizeof(double) * fN, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(st + fN, u, sizeof(double) * 3 * fN, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && pi)
+            e = cudaMemcpyAsync(st + 4 * fN, pi, sizeof(double) * 6 * fN, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = tslb::launch_encode(h, st, st + fN, pi ? st + 4 * fN : nullptr, h->buf[h->cur], p);
+        cudaFreeAsync(st, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "init copy / encode");
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "init synchronize");
+    h->t = 0;
+    drop_checkpoints(h);
+    return TSLB_OK;
+}
+
+int tslb_set_force_field(tslb_t* h, const float* F, int where) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    cudaSetDevice(h->device);
+    if (!F) {
+        if (h->force_field) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->force_field);
+        }
+        h->force_field = nullptr;
+        return TSLB_OK;
+    }
+    const tslb::Geometry& g = h->g;
+    cudaError_t e;
+    if (!h->force_field) {
+        e = dev_alloc((void**)&h->force_field, sizeof(float) * 3 * g.fstride);
+        if (e != cudaSuccess) {
+            h->force_field = nullptr;
+            return fail(h, TSLB_ERR_ALLOC, "force field allocation failed");
+        }
+    }
+    // Gather the interior of the full-lattice [3][N] array row by row.
+    const long long fnx = h->dims[0], fny = h->dims[1], fN = fnx * fny * h->dims[2];
+    const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    for (int a = 0; a < 3; ++a) {
+        const float* srcA = F + a * fN;
+        float* dstA = h->force_field + a * g.fstride;
+        for (int z = 0; z < g.nz; ++z) {
+            const float* s = srcA + g.lo[0] + fnx * (g.lo[1] + fny * (long long)(z + g.lo[2]));
+            e = cudaMemcpy2DAsync(dstA + g.plane * z, sizeof(float) * g.nx, s, sizeof(float) * fnx,
+                                  sizeof(float) * g.nx, g.ny, kind, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "force field copy");
+        }
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "force field synchronize");
+    return TSLB_OK;
+}
+
+int tslb_step(tslb_t* h, int64_t nsteps) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (nsteps < 0) return fail(h, TSLB_ERR_INVALID, "nsteps < 0");
+    cudaSetDevice(h->device);
+    if (h->kernel == TSLB_KERNEL_FACTORED && !tslb::factored_supports(h))
+        return fail(h, TSLB_ERR_UNSUPPORTED, "the factored kernel does not support this configuration");
+    const int k = h->checkpoint_every;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e;
+        if (k > 0 && h->t % k == 0 && (int64_t)h->ckpts.size() == h->t / k) {
+            void* c = nullptr;
+            e = dev_alloc(&c, state_bytes(h));
+            if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "checkpoint allocation failed");
+            h->ckpts.push_back(c);
+            e = cudaMemcpyAsync(c, h->buf[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint copy");
+        }
+        const tslb::Physics p = tslb::make_physics(h);
+        e = tslb::launch_step_any(h, h->buf[h->cur], h->buf[h->cur ^ 1], p);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return TSLB_OK;
+}
+
+int tslb_get_moments(tslb_t* h, double* rho, double* u, double* pi, int where) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    cudaSetDevice(h->device);
+    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
+    const tslb::Physics p = tslb::make_physics(h);
+    cudaError_t e;
+    if (where == TSLB_DEVICE) {
+        e = tslb::launch_decode(h, h->buf[h->cur], rho, u, pi, p);
+        if (e != cudaSuccess) return cuda_fail(h, e, "decode launch");
+    } else {
+        double* st = nullptr;
+        e = dev_alloc_async((void**)&st, sizeof(double) * (size_t)fN * 10, h->stream);
+        if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "staging allocation failed");
+        e = tslb::launch_decode(h, h->buf[h->cur], rho ? st : nullptr, u ? st + fN : nullptr,
+                                pi ? st + 4 * fN : nullptr, p);
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(rho, st, sizeof(double) * fN, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && u)
+            e = cudaMemcpyAsync(u, st + fN, sizeof(double) * 3 * fN, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && pi)
+            e = cudaMemcpyAsync(pi, st + 4 * fN, sizeof(double) * 6 * fN, cudaMemcpyDeviceToHost, h->stream);
+        cudaFreeAsync(st, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get copy / decode");
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get synchronize");
+    return TSLB_OK;
+}
+
+int tslb_diagnostics(tslb_t* h, tslb_diag* out) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (!out) return fail(h, TSLB_ERR_INVALID, "null output");
+    cudaSetDevice(h->device);
+    const tslb::Physics p = tslb::make_physics(h);
+    double* dev_out = h->diag_part + 8 * h->diag_blocks;
+    cudaError_t e = tslb::launch_diag(h, h->buf[h->cur], p, dev_out);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->diag_host, dev_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
+    const double* d = h->diag_host;
+    out->mass = d[0];
+    out->momentum[0] = d[1];
+    out->momentum[1] = d[2];
+    out->momentum[2] = d[3];
+    out->kinetic_energy = d[4];
+    const bool ywalls = h->bc[2] == TSLB_BC_BOUNCEBACK;
+    out->wall_shear = ywalls ? d[5] / (2.0 * (double)h->g.nx * (double)h->g.nz) : 0.0;
+    out->max_speed = d[6];
+    out->nonfinite = (int64_t)d[7];
+    out->steps = h->t;
+    out->nodes = (int64_t)h->g.plane * h->g.nz;
+    if (out->nonfinite > 0) return fail(h, TSLB_ERR_UNSTABLE, "NaN or Inf in the moment fields");
+    return TSLB_OK;
+}
+
+int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (!dJdF) return fail(h, TSLB_ERR_INVALID, "null output");
+    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    cudaSetDevice(h->device);
+    std::string msg;
+    const int r = tslb::adjoint_force_gradient(h, nsteps, dJdF, where, &msg);
+    if (r != TSLB_OK) return fail(h, r, msg);
+    return TSLB_OK;
+}
+
+int64_t tslb_interior_nodes(const tslb_t* h) { return h ? (int64_t)h->g.plane * h->g.nz : 0; }
+
+int tslb_synchronize(tslb_t* h) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+    return TSLB_OK;
+}
+
+void tslb_destroy(tslb_t* h) { release(h); }
+
+const char* tslb_last_error(const tslb_t* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// Internal declarations of the TSLB CUDA library: handle layout, storage
+// codecs and the per-node Hermite algebra shared by the step kernels.
+//
+// Notation follows arXiv 2401.17074, Sec. 2.  The post-collision population
+// leaving a node (Eq. LBexp with Eq. eqts and Eq. noneqts, plus the Luo force
+// term of Sec. 3.1) is written in the D1Q3 x D1Q3 x D1Q3 tensor-product
+// Hermite basis.  With
+//     rho = 1 + drho, j = rho (u + F), P = (1 - omega) Pi^neq,
+//     h2_ab  = rho u_a u_b + P_ab,
+//     h3_abg = rho u_a u_b u_g + u_a P_bg + u_b P_ag + u_g P_ab,
+// the deviation from the rest population is
+//     f_i - w_i = (1/216) * W(c_i) * sum_k A_k phi_k1(c_ix) phi_k2(c_iy) phi_k3(c_iz),
+// with integer 1-D weights W = {1, 4, 1} (= 6 w), integer 1-D Hermite values
+// phi_0 = 1, phi_1 = c, phi_2 = 3c^2 - 1 (= 3 (c^2 - cs^2)), and the 17 modes
+// the D3Q27 lattice supports up to third order:
+//     A_000 = drho,  A_a = 3 j_a,  A_aa = 1.5 h2_aa,  A_ab = 9 h2_ab,
+//     A_aab = 4.5 h3_aab,  A_xyz = 27 h3_xyz
+// (the xxx-type third-order Hermite polynomials vanish on D3Q27).  Every
+// constant in the reconstruction, streaming and moment sums is then an exact
+// binary number, so the discrete moment identities hold exactly in FP32 and
+// mass and momentum are not rescaled by rounded lattice constants each step;
+// the kernels accumulate 216 x the deviation moments and divide once at the end.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/tslb.h"
+
+namespace tslb {
+
+// Field order of the stored moments.
+enum Field { F_DRHO = 0, F_UX, F_UY, F_UZ, F_PXX, F_PYY, F_PZZ, F_PXY, F_PXZ, F_PYZ, NFIELDS };
+
+// Mode order of the 17 Hermite coefficients (k1 k2 k3 digits = phi order per axis).
+enum Mode {
+    M000 = 0,
+    M100, M010, M001,
+    M200, M020, M002,
+    M110, M101, M011,
+    M210, M201, M120, M021, M102, M012,
+    M111,
+    NMODES
+};
+
+// Geometry of the stored interior box and its faces, passed by value to kernels.
+struct Geometry {
+    int nx, ny, nz;        // interior extents (stored)
+    int lo[3];             // lattice coordinate of interior index 0 per axis (0 or 1)
+    int bc[6];             // face codes
+    long long fstride;     // elements between consecutive fields
+    long long plane;       // nx * ny
+};
+
+struct Physics {
+    float omega1;          // 1 - omega
+    float F[3];            // constant acceleration
+    const float* force;    // per-node acceleration [3][fstride] or nullptr
+    // inflow (z- face)
+    long long in_c2[2];
+    long long in_d;
+    float in_u;
+    float in_amp;
+    unsigned long long in_seed;
+    long long t;           // step index of the state being read
+    // storage scales (16-bit codecs): value = stored * scale
+    float s_u, s_pi, inv_s_u, inv_s_pi;
+};
+
+// ---- storage codecs --------------------------------------------------------
+struct CodecF32 {
+    typedef float T;
+    static __device__ __forceinline__ float load(const float* p, float) { return __ldg(p); }
+    static __device__ __forceinline__ float dec(float v, float) { return v; }
+    static __device__ __forceinline__ float enc(float v, float) { return v; }
+};
+struct CodecBF16 {
+    typedef __nv_bfloat16 T;
+    static __device__ __forceinline__ float dec(T v, float s) { return __bfloat162float(v) * s; }
+    static __device__ __forceinline__ T enc(float v, float inv_s) { return __float2bfloat16_rn(v * inv_s); }
+};
+struct CodecF16 {
+    typedef __half T;
+    static __device__ __forceinline__ float dec(T v, float s) { return __half2float(v) * s; }
+    static __device__ __forceinline__ T enc(float v, float inv_s) { return __float2half_rn(v * inv_s); }
+};
+
+// Scale of field f under the 16-bit codecs (drho unscaled).
+__device__ __forceinline__ float field_scale(int f, const Physics& p) {
+    return f == F_DRHO ? 1.0f : (f <= F_UZ ? p.s_u : p.s_pi);
+}
+__device__ __forceinline__ float field_inv_scale(int f, const Physics& p) {
+    return f == F_DRHO ? 1.0f : (f <= F_UZ ? p.inv_s_u : p.inv_s_pi);
+}
+
+// ---- Hermite algebra -------------------------------------------------------
+constexpr float CS2 = 1.0f / 3.0f;
+
+// Mode coefficients (deviation form) of the post-collision population.
+// (rho-1, u) enter the equilibrium part, (v, Pi) the non-equilibrium part
+// (v = u everywhere except the inflow ghost layer of Eq. neq_final).
+__device__ __forceinline__ void post_modes(float drho, float ux, float uy, float uz, float vx, float vy, float vz,
+                                           const float pi[6], float jx_add, float jy_add, float jz_add,
+                                           float omega1, float A[NMODES]) {
+    const float rho = 1.0f + drho;
+    const float pxx = omega1 * pi[0], pyy = omega1 * pi[1], pzz = omega1 * pi[2];
+    const float pxy = omega1 * pi[3], pxz = omega1 * pi[4], pyz = omega1 * pi[5];
+    const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
+    const float h2xx = fmaf(rux, ux, pxx), h2yy = fmaf(ruy, uy, pyy), h2zz = fmaf(ruz, uz, pzz);
+    const float qxy = rux * uy, qxz = rux * uz, qyz = ruy * uz;  // rho u_a u_b
+    const float h2xy = qxy + pxy, h2xz = qxz + pxz, h2yz = qyz + pyz;
+    // h3_aab = rho u_a u_a u_b + 2 v_a P_ab + v_b P_aa
+    const float h3xxy = fmaf(qxy, ux, fmaf(2.0f * vx, pxy, vy * pxx));
+    const float h3xxz = fmaf(qxz, ux, fmaf(2.0f * vx, pxz, vz * pxx));
+    const float h3xyy = fmaf(qxy, uy, fmaf(2.0f * vy, pxy, vx * pyy));
+    const float h3yyz = fmaf(qyz, uy, fmaf(2.0f * vy, pyz, vz * pyy));
+    const float h3xzz = fmaf(qxz, uz, fmaf(2.0f * vz, pxz, vx * pzz));
+    const float h3yzz = fmaf(qyz, uz, fmaf(2.0f * vz, pyz, vy * pzz));
+    const float h3xyz = fmaf(qxy, uz, fmaf(vx, pyz, fmaf(vy, pxz, vz * pxy)));
+    A[M000] = drho;
+    A[M100] = 3.0f * fmaf(rho, jx_add, rux);
+    A[M010] = 3.0f * fmaf(rho, jy_add, ruy);
+    A[M001] = 3.0f * fmaf(rho, jz_add, ruz);
+    A[M200] = 1.5f * h2xx;
+    A[M020] = 1.5f * h2yy;
+    A[M002] = 1.5f * h2zz;
+    A[M110] = 9.0f * h2xy;
+    A[M101] = 9.0f * h2xz;
+    A[M011] = 9.0f * h2yz;
+    A[M210] = 4.5f * h3xxy;
+    A[M201] = 4.5f * h3xxz;
+    A[M120] = 4.5f * h3xyy;
+    A[M021] = 4.5f * h3yyz;
+    A[M102] = 4.5f * h3xzz;
+    A[M012] = 4.5f * h3yzz;
+    A[M111] = 27.0f * h3xyz;
+}
+
+// Integer 1-D Hermite values and weights of the scaled basis above.
+__host__ __device__ __forceinline__ float phi(int k, int c) {
+    return k == 0 ? 1.0f : (k == 1 ? (float)c : (float)(3 * c * c - 1));
+}
+__host__ __device__ __forceinline__ float wgt(int c) { return c == 0 ? 4.0f : 1.0f; }
+
+// Mode digits (k1, k2, k3) per mode index.
+__host__ __device__ __forceinline__ void mode_digits(int m, int& k1, int& k2, int& k3) {
+    const unsigned char d[NMODES][3] = {
+        {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1},
+        {0, 1, 1}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1}};
+    k1 = d[m][0]; k2 = d[m][1]; k3 = d[m][2];
+}
+
+// 216 x (f_i - w_i) along c = (cx, cy, cz) from the scaled mode coefficients.
+__device__ __forceinline__ float pop_dev216(const float A[NMODES], int cx, int cy, int cz) {
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 0; m < NMODES; ++m) {
+        int k1, k2, k3;
+        mode_digits(m, k1, k2, k3);
+        s = fmaf(A[m], phi(k1, cx) * phi(k2, cy) * phi(k3, cz), s);
+    }
+    return wgt(cx) * wgt(cy) * wgt(cz) * s;
+}
+
+// New moments from the 216-scaled deviation sums D0 = 216 drho',
+// J = 216 j', S_ab = 216 (sum f c_a c_b - cs^2 delta_ab) (Sec. 2.1):
+//   drho' = D0/216, u' = J/(216 + D0),
+//   Pi'_ab = (S_ab - J_a u'_b - delta_ab D0/3) / 216.
+// Division by 216 uses a two-term constant so that it is correctly rounded
+// up to ties; the reciprocal of 216 + D0 is correctly rounded.
+constexpr float INV216_HI = 0x1.2f684cp-8f;    // fl(1/216)
+constexpr float INV216_LO = -0x1.2f684cp-35f;  // 1/216 - INV216_HI (exact)
+__device__ __forceinline__ float div216(float x) { return fmaf(x, INV216_HI, x * INV216_LO); }
+
+__device__ __forceinline__ void finish_moments(float D0, const float J[3], const float S[6], float out[NFIELDS]) {
+    const float inv = __frcp_rn(216.0f + D0);
+    const float ux = J[0] * inv, uy = J[1] * inv, uz = J[2] * inv;
+    const float d3 = D0 * (1.0f / 3.0f);
+    out[F_DRHO] = div216(D0);
+    out[F_UX] = ux;
+    out[F_UY] = uy;
+    out[F_UZ] = uz;
+    out[F_PXX] = div216(S[0] - fmaf(J[0], ux, d3));
+    out[F_PYY] = div216(S[1] - fmaf(J[1], uy, d3));
+    out[F_PZZ] = div216(S[2] - fmaf(J[2], uz, d3));
+    out[F_PXY] = div216(S[3] - J[0] * uy);
+    out[F_PXZ] = div216(S[4] - J[0] * uz);
+    out[F_PYZ] = div216(S[5] - J[1] * uz);
+}
+
+// Philox4x32-10 (Salmon et al., SC'11) for the inflow noise.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+// Imposed inflow velocity u_z at lattice column (x, y) for step t.
+__device__ __forceinline__ float inflow_uz(const Physics& p, long long x, long long y) {
+    const long long dx = 2 * x - p.in_c2[0], dy = 2 * y - p.in_c2[1];
+    if (dx * dx + dy * dy > p.in_d * p.in_d) return 0.0f;
+    uint32_t c[4] = {(uint32_t)x, (uint32_t)y, (uint32_t)p.t, 0u};
+    philox4x32_10(c, (uint32_t)p.in_seed, (uint32_t)(p.in_seed >> 32));
+    const float xi = (float)(c[0] >> 8) * (1.0f / 8388608.0f) - 1.0f;
+    return p.in_u * (1.0f + p.in_amp * xi);
+}
+
+}  // namespace tslb
+
+// ---- handle -----------------------------------------------------------------
+struct tslb_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t dims[3] = {0, 0, 0};
+    int bc[6] = {0, 0, 0, 0, 0, 0};
+    tslb::Geometry g{};
+    double tau = 1.0, omega = 1.0;
+    double force[3] = {0, 0, 0};
+    int precision = TSLB_FP32;
+    double u_ref = 0.05, pi_ref = 1e-3;
+    int kernel = TSLB_KERNEL_AUTO;
+    int checkpoint_every = 0;
+    tslb_inflow inflow{};
+    size_t elem = 4;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    float* force_field = nullptr;
+    int64_t t = 0;
+    // diagnostics scratch
+    double* diag_part = nullptr;
+    int diag_blocks = 0;
+    double* diag_host = nullptr;
+    // adjoint checkpoints: ckpts[s] holds the moments at step s * checkpoint_every
+    std::vector<void*> ckpts;
+    std::string err;
+};
+
+namespace tslb {
+
+// Launchers implemented in the kernel translation units.
+cudaError_t launch_step_direct(const tslb_s* h, const void* src, void* dst, const Physics& p);
+cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p);
+// The step kernel tslb_step uses for this handle (same choice, bitwise-identical results).
+cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p);
+bool use_factored(const tslb_s* h);
+int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, std::string* msg);
+bool factored_supports(const tslb_s* h);
+cudaError_t launch_encode(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst,
+                          const Physics& p);
+cudaError_t launch_decode(const tslb_s* h, const void* src, double* rho, double* u, double* pi, const Physics& p);
+cudaError_t launch_diag(const tslb_s* h, const void* src, const Physics& p, double* out_dev);
+
+Physics make_physics(const tslb_s* h);
+
+}  // namespace tslb

@@ -93,7 +93,7 @@ def shear_wave(dims, amp, tau, axis_u=0, axis_k=1, mode=1):
     return _pack(rho, u, pi)
 
 
-# ---- turbulent channel (Sec. 3.1 shape; BASELINE channel: 512 x 130 x 256) --
+# ---- turbulent channel (Sec. 3.1 shape; benchmark grid 512 x 130 x 256) -----
 
 def channel_params(nx=512, ny=130, nz=256, u_tau=0.0035, tau=0.503, re_tau=180.0):
     """Walls at y = 0 and y = ny-1 (solid layers, halfway bounce-back), H = (ny-2)/2.
@@ -141,7 +141,7 @@ def channel_state(prm, seed=1, noise=0.02):
     return _pack(rho, u, [zero, zero, zero, pxy, zero, zero])
 
 
-# ---- round jet (Sec. 3.2 shape; BASELINE jet: 256 x 256 x 640, Re = 7000) ----
+# ---- round jet (Sec. 3.2 shape; grid 256 x 256 x 640, Re = 7000) ------------
 
 def jet_params(nx=256, ny=256, nz=640, D=20, u_jet=0.05, re=7000.0, noise_amp=0.01, seed=3):
     """Inflow z = 0 (Hermite-NEE ghost), outflow z = nz-1, free-slip x and y walls.

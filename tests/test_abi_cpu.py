@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+symbol declared in include/tslb.h, and argument validation rejects bad
+requests before any CUDA call (so these run without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2401_17074_b300 as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "tslb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(tslb_[a-z_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_abi():
+    names = _declared_functions()
+    assert set(names) == set(T.EXPORTED), names
+
+
+def test_library_exports_every_declared_symbol():
+    path = T._build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in _declared_functions():
+        assert name in exported, name
+    L = T.load()
+    for name in _declared_functions():
+        assert hasattr(L, name)
+
+
+def test_library_targets_sm_103a():
+    path = T._build.build()
+    out = subprocess.run(["cuobjdump", "--list-elf", path], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_options_default():
+    o = T.tslb_options_default()
+    assert o.precision == T.FP32 and abs(o.u_ref - 0.05) < 1e-15 and o.kernel == T.KERNEL_AUTO
+
+
+def _create_code(dims=(8, 8, 8), tau=0.6, bc=(0,) * 6, lattice=T.TSLB_D3Q27, opt=None):
+    L = T.load()
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * 3)(*dims)
+    b = (ctypes.c_int * 6)(*bc)
+    code = L.tslb_create(ctypes.byref(h), lattice, d, tau, None, b, ctypes.byref(opt) if opt else None)
+    return code, h
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(tau=0.5), T.TSLB_ERR_INVALID),
+    (dict(tau=0.3), T.TSLB_ERR_INVALID),
+    (dict(tau=float("nan")), T.TSLB_ERR_INVALID),
+    (dict(lattice=19), T.TSLB_ERR_UNSUPPORTED),
+    (dict(dims=(2, 8, 8)), T.TSLB_ERR_INVALID),
+    (dict(dims=(8, 3, 8), bc=(0, 0, 1, 1, 0, 0)), T.TSLB_ERR_INVALID),
+    (dict(bc=(0, 0, 1, 0, 0, 0)), T.TSLB_ERR_INVALID),
+    (dict(bc=(1, 1, 0, 0, 0, 0)), T.TSLB_ERR_UNSUPPORTED),
+    (dict(bc=(0, 0, 0, 0, 4, 3)), T.TSLB_ERR_UNSUPPORTED),
+    (dict(bc=(0, 0, 1, 1, 3, 4)), T.TSLB_ERR_UNSUPPORTED),
+    (dict(bc=(0, 0, 9, 9, 0, 0)), T.TSLB_ERR_INVALID),
+])
+def test_create_rejects_bad_arguments(kw, code):
+    c, h = _create_code(**kw)
+    assert c == code
+    assert not h.value  # *out untouched
+    assert len(T.tslb_last_error(None)) > 0
+
+
+def test_bad_option_values_rejected():
+    o = T.tslb_options_default()
+    o.precision = 7
+    c, h = _create_code(opt=o)
+    assert c == T.TSLB_ERR_INVALID
+    o = T.tslb_options_default()
+    o.precision = T.BF16
+    o.u_ref = 0.0
+    c, h = _create_code(opt=o)
+    assert c == T.TSLB_ERR_INVALID
+
+
+def test_null_handle_calls_fail_cleanly():
+    L = T.load()
+    assert L.tslb_step(None, 1) == T.TSLB_ERR_INVALID
+    assert L.tslb_synchronize(None) == T.TSLB_ERR_INVALID
+    assert L.tslb_interior_nodes(None) == 0
+    L.tslb_destroy(None)
