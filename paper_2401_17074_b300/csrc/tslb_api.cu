@@ -42,6 +42,20 @@ cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t s) {
 
 bool valid_handle(const tslb_s* h) { return h != nullptr; }
 
+// After a synchronise: report a bounded device wait that gave up (the kernel
+// then skipped the rest of its work), and clear the word.
+int check_device_status(tslb_s* h) {
+    int v = 0;
+    if (!h->dev_err) return TSLB_OK;
+    cudaError_t e = cudaMemcpy(&v, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (v != 0) {
+        cudaMemset(h->dev_err, 0, sizeof(int));
+        return fail(h, TSLB_ERR_CUDA, "a bounded device wait gave up; the step results are invalid");
+    }
+    return TSLB_OK;
+}
+
 void release(tslb_s* h) {
     if (!h) return;
     cudaSetDevice(h->device);
@@ -50,6 +64,7 @@ void release(tslb_s* h) {
         if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->force_field) cudaFree(h->force_field);
     if (h->diag_part) cudaFree(h->diag_part);
+    if (h->dev_err) cudaFree(h->dev_err);
     if (h->diag_host) cudaFreeHost(h->diag_host);
     for (void* c : h->ckpts) cudaFree(c);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -72,6 +87,7 @@ Physics make_physics(const tslb_s* h) {
     p.in_amp = (float)h->inflow.noise_amp;
     p.in_seed = h->inflow.seed;
     p.t = h->t;
+    p.err = h->dev_err;
     if (h->precision == TSLB_FP32) {
         p.s_u = p.s_pi = p.inv_s_u = p.inv_s_pi = 1.0f;
     } else {
@@ -153,7 +169,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_INVALID, "unknown precision");
     if (o.precision != TSLB_FP32 && (!(o.u_ref > 0) || !(o.pi_ref > 0)))
         return fail(nullptr, TSLB_ERR_INVALID, "16-bit storage needs positive u_ref and pi_ref");
-    if (o.kernel < TSLB_KERNEL_AUTO || o.kernel > TSLB_KERNEL_FACTORED)
+    if (o.kernel < TSLB_KERNEL_AUTO || o.kernel > TSLB_KERNEL_FACTORED_TMA)
         return fail(nullptr, TSLB_ERR_INVALID, "unknown kernel choice");
     if (o.checkpoint_every < 0) return fail(nullptr, TSLB_ERR_INVALID, "checkpoint_every < 0");
     if (bz0 == TSLB_BC_INFLOW && o.inflow.diameter < 0) return fail(nullptr, TSLB_ERR_INVALID, "bad inflow diameter");
@@ -227,8 +243,11 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     }
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->sm_count = sms;
     h->diag_blocks = sms * 4;
     e = dev_alloc((void**)&h->diag_part, sizeof(double) * 8 * (h->diag_blocks + 1));
+    if (e == cudaSuccess) e = dev_alloc((void**)&h->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->diag_host, sizeof(double) * 8);
     if (e != cudaSuccess) {
         std::string m = std::string("device allocation of the diagnostics scratch failed: ") + cudaGetErrorString(e);
@@ -319,7 +338,7 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (nsteps < 0) return fail(h, TSLB_ERR_INVALID, "nsteps < 0");
     cudaSetDevice(h->device);
-    if (h->kernel == TSLB_KERNEL_FACTORED && !tslb::factored_supports(h))
+    if ((h->kernel == TSLB_KERNEL_FACTORED || h->kernel == TSLB_KERNEL_FACTORED_TMA) && !tslb::factored_supports(h))
         return fail(h, TSLB_ERR_UNSUPPORTED, "the factored kernel does not support this configuration");
     const int k = h->checkpoint_every;
     for (int64_t s = 0; s < nsteps; ++s) {
@@ -368,7 +387,7 @@ int tslb_get_moments(tslb_t* h, double* rho, double* u, double* pi, int where) {
     }
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "get synchronize");
-    return TSLB_OK;
+    return check_device_status(h);
 }
 
 int tslb_diagnostics(tslb_t* h, tslb_diag* out) {
@@ -381,6 +400,8 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->diag_host, dev_out, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
+    const int st = check_device_status(h);
+    if (st != TSLB_OK) return st;
     const double* d = h->diag_host;
     out->mass = d[0];
     out->momentum[0] = d[1];
@@ -415,7 +436,7 @@ int tslb_synchronize(tslb_t* h) {
     cudaSetDevice(h->device);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
-    return TSLB_OK;
+    return check_device_status(h);
 }
 
 void tslb_destroy(tslb_t* h) { release(h); }

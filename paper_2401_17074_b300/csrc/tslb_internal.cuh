@@ -29,7 +29,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/tslb.h"
+#include "tslb.h"
 
 namespace tslb {
 
@@ -67,6 +67,7 @@ struct Physics {
     float in_amp;
     unsigned long long in_seed;
     long long t;           // step index of the state being read
+    int* err;              // device status word: nonzero after a bounded wait gave up
     // storage scales (16-bit codecs): value = stored * scale
     float s_u, s_pi, inv_s_u, inv_s_pi;
 };
@@ -171,13 +172,22 @@ __device__ __forceinline__ float pop_dev216(const float A[NMODES], int cx, int c
 //   drho' = D0/216, u' = J/(216 + D0),
 //   Pi'_ab = (S_ab - J_a u'_b - delta_ab D0/3) / 216.
 // Division by 216 uses a two-term constant so that it is correctly rounded
-// up to ties; the reciprocal of 216 + D0 is correctly rounded.
+// up to ties; the reciprocal of 216 + D0 is refined to about half an ulp.
 constexpr float INV216_HI = 0x1.2f684cp-8f;    // fl(1/216)
 constexpr float INV216_LO = -0x1.2f684cp-35f;  // 1/216 - INV216_HI (exact)
 __device__ __forceinline__ float div216(float x) { return fmaf(x, INV216_HI, x * INV216_LO); }
 
+// 1/r for r = 216 + D0 (a normal number near 216): hardware reciprocal plus
+// one Newton step, accurate to about half an ulp.
+__device__ __forceinline__ float rcp_refined(float r) {
+    float i;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(i) : "f"(r));
+    const float e = fmaf(-r, i, 1.0f);
+    return fmaf(i, e, i);
+}
+
 __device__ __forceinline__ void finish_moments(float D0, const float J[3], const float S[6], float out[NFIELDS]) {
-    const float inv = __frcp_rn(216.0f + D0);
+    const float inv = rcp_refined(216.0f + D0);
     const float ux = J[0] * inv, uy = J[1] * inv, uz = J[2] * inv;
     const float d3 = D0 * (1.0f / 3.0f);
     out[F_DRHO] = div216(D0);
@@ -229,6 +239,8 @@ struct tslb_s {
     int precision = TSLB_FP32;
     double u_ref = 0.05, pi_ref = 1e-3;
     int kernel = TSLB_KERNEL_AUTO;
+    int sm_count = 148;
+    int* dev_err = nullptr;  // device status word of the bounded waits
     int checkpoint_every = 0;
     tslb_inflow inflow{};
     size_t elem = 4;
@@ -253,6 +265,7 @@ cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, co
 // The step kernel tslb_step uses for this handle (same choice, bitwise-identical results).
 cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p);
 bool use_factored(const tslb_s* h);
+bool factored_uses_tma(const tslb_s* h);
 int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, std::string* msg);
 bool factored_supports(const tslb_s* h);
 cudaError_t launch_encode(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst,
