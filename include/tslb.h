@@ -159,6 +159,39 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out);
  * array (boundary entries 0).  Synchronises the stream. */
 int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where);
 
+/* ---- Diagnostics without allocation ------------------------------------
+ * The paper has no counterpart of this call.  It serves callers that must not
+ * allocate device memory at the point where they want the numbers: code that
+ * runs while its stream is being captured into a CUDA graph (allocation calls
+ * are not allowed inside a capture), real-time loops that forbid allocator
+ * calls, or programs whose framework allocator has already reserved the
+ * device memory.
+ *
+ * tslb_diagnostics_noalloc computes the same FP64 sums as tslb_diagnostics
+ * over moment arrays the caller owns: rho[N], u[3][N] and pi[6][N] (pi may be
+ * NULL) in the full-lattice FP64 layout that tslb_get_moments(..., TSLB_DEVICE)
+ * writes, in device memory of the current device.  dims and bc describe the
+ * lattice as for tslb_create (only interior nodes are summed); tau sets the
+ * wall-shear factor (1 - 1/(2 tau)).  It launches two kernels on `stream`
+ * (NULL = the default stream) and returns without synchronising; `out` (device
+ * memory, 8 doubles) then holds mass, momentum x, y, z, kinetic energy, wall
+ * shear, max |u| and the number of interior nodes with a NaN/Inf value.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the per-block
+ * partial sums live in a fixed 256 KB __device__ array that every device
+ * loading this library holds until the process exits.  Consequences:
+ *   - at most TSLB_NOALLOC_MAX_NODES interior nodes; more return TSLB_ERR_INVALID;
+ *   - the first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress, with that device current; make that first call
+ *     before any stream capture;
+ *   - every call shares the array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and give wrong sums.  Each call
+ *     rewrites every partial it reads, so nothing carries over between calls.
+ * Errors return a negative tslb_status; tslb_last_error(NULL) explains. */
+#define TSLB_NOALLOC_MAX_NODES ((int64_t)1 << 26)
+int tslb_diagnostics_noalloc(const double* rho, const double* u, const double* pi, const int64_t dims[3],
+                             const int bc[6], double tau, void* stream, double* out);
+
 /* Number of interior (updated) nodes. */
 int64_t tslb_interior_nodes(const tslb_t* h);
 

@@ -30,8 +30,9 @@ KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED, KERNEL_FACTORED_TMA = 0, 1, 2, 3
 EXPORTED = [
     "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_set_force_field", "tslb_step",
     "tslb_get_moments", "tslb_diagnostics", "tslb_adjoint_force_gradient", "tslb_interior_nodes",
-    "tslb_synchronize", "tslb_destroy", "tslb_last_error",
+    "tslb_synchronize", "tslb_destroy", "tslb_last_error", "tslb_diagnostics_noalloc",
 ]
+NOALLOC_MAX_NODES = 1 << 26
 
 
 class tslb_inflow(ctypes.Structure):
@@ -90,6 +91,8 @@ def load(build_if_missing=True):
     L.tslb_destroy.restype = None
     L.tslb_last_error.argtypes = [vp]
     L.tslb_last_error.restype = ctypes.c_char_p
+    L.tslb_diagnostics_noalloc.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.c_double, vp, vp]
     _lib = L
     return L
 
@@ -187,6 +190,21 @@ def tslb_diagnostics(h):
 def tslb_adjoint_force_gradient(h, nsteps, dJdF, where=HOST):
     p = ctypes.c_void_p(dJdF.data_ptr() if hasattr(dJdF, "data_ptr") else dJdF.ctypes.data)
     _check(load().tslb_adjoint_force_gradient(h, int(nsteps), p, int(where)), h)
+
+
+def tslb_diagnostics_noalloc(rho, u, pi, dims, bc, tau, out, stream=None):
+    """FP64 diagnostics of caller-owned device moment arrays without any allocation.
+
+    rho, u, pi: CUDA float64 tensors in the full-lattice layout of
+    tslb_get_moments; out: CUDA float64 tensor of 8 entries.  Asynchronous on
+    `stream` (a raw cudaStream_t value, None = default stream).
+    """
+    def p(a):
+        return None if a is None else ctypes.c_void_p(a.data_ptr())
+    d = (ctypes.c_int64 * 3)(*[int(v) for v in dims])
+    b = (ctypes.c_int * 6)(*[int(v) for v in bc])
+    s = ctypes.c_void_p(int(stream)) if stream else None
+    _check(load().tslb_diagnostics_noalloc(p(rho), p(u), p(pi), d, b, float(tau), s, p(out)), None)
 
 
 def tslb_interior_nodes(h):

@@ -14,6 +14,7 @@ SOURCES = [
     "tslb_step_direct.cu",
     "tslb_step_factored.cu",
     "tslb_adjoint.cu",
+    "tslb_noalloc.cu",
 ]
 
 NVCC_FLAGS = [

@@ -75,6 +75,8 @@ void release(tslb_s* h) {
 
 namespace tslb {
 
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+
 Physics make_physics(const tslb_s* h) {
     Physics p{};
     p.omega1 = (float)(1.0 - h->omega);

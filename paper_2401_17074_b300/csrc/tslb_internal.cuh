@@ -274,5 +274,7 @@ cudaError_t launch_decode(const tslb_s* h, const void* src, double* rho, double*
 cudaError_t launch_diag(const tslb_s* h, const void* src, const Physics& p, double* out_dev);
 
 Physics make_physics(const tslb_s* h);
+// Error text reported by tslb_last_error(NULL) on this thread.
+void set_global_error(const std::string& msg);
 
 }  // namespace tslb
