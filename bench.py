@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="tslb", choices=["tslb", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "factored", "factored_tma"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "direct", "factored"])
     ap.add_argument("--nx", type=int, default=512)
     ap.add_argument("--ny", type=int, default=130)
     ap.add_argument("--nz", type=int, default=256)
@@ -287,8 +287,7 @@ def main():
         torch.cuda.set_device(0)
     import paper_2401_17074_b300 as T
     T.load()
-    kernel = {"auto": T.KERNEL_AUTO, "direct": T.KERNEL_DIRECT, "factored": T.KERNEL_FACTORED,
-              "factored_tma": T.KERNEL_FACTORED_TMA}[args.kernel]
+    kernel = {"auto": T.KERNEL_AUTO, "direct": T.KERNEL_DIRECT, "factored": T.KERNEL_FACTORED}[args.kernel]
     prm, state = make_state(args.nx, args.ny, args.nz)
     stream = torch.cuda.Stream()
     hbm, hbm_src = measured_peaks()
@@ -302,8 +301,7 @@ def main():
     bpn = BYTES_PER_NODE[args.precision]
     achieved = bpn * nodes / launch_s / 1e9
     from paper_2401_17074_b300 import build as B
-    kname = {T.KERNEL_DIRECT: "tslb_step_direct", T.KERNEL_FACTORED_TMA: "tslb_step_factored_tma"}.get(
-        kernel, "tslb_step_factored")
+    kname = "tslb_step_direct" if kernel == T.KERNEL_DIRECT else "tslb_step_factored"
     traffic = traffic_record(kname, args.precision)
 
     variants = {}

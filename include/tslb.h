@@ -75,9 +75,7 @@ typedef enum tslb_where { TSLB_HOST = 0, TSLB_DEVICE = 1 } tslb_where;
 typedef enum tslb_kernel {
     TSLB_KERNEL_AUTO = 0,     /* the fastest kernel that supports the configuration */
     TSLB_KERNEL_DIRECT = 1,   /* one thread per node, 27 direct gathers (cross-check path) */
-    TSLB_KERNEL_FACTORED = 2,    /* sum-factorised, z-marching tiled kernel, register-prefetched loads */
-    TSLB_KERNEL_FACTORED_TMA = 3 /* the same kernel fed through a TMA shared-memory ring (row pitch a
-                                    multiple of 16 bytes; otherwise it runs the register-prefetch feed) */
+    TSLB_KERNEL_FACTORED = 2  /* sum-factorised, z-marching tiled kernel */
 } tslb_kernel;
 
 /* Inflow nozzle of the round jet (Sec. 3.2): inside the disc

@@ -25,7 +25,7 @@ TSLB_D3Q27 = 27
 PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
 FP32, BF16, FP16 = 0, 1, 2
 HOST, DEVICE = 0, 1
-KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED, KERNEL_FACTORED_TMA = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED = 0, 1, 2
 
 EXPORTED = [
     "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_set_force_field", "tslb_step",

@@ -22,8 +22,7 @@ namespace {
 template <class Codec>
 __device__ __forceinline__ void load_m(const typename Codec::T* __restrict__ src, long long fs, long long idx,
                                        const Physics& p, float m[NFIELDS]) {
-#pragma unroll
-    for (int f = 0; f < NFIELDS; ++f) m[f] = Codec::dec(src[f * fs + idx], field_scale(f, p));
+    NodeIO<Codec>::load(src, fs, idx, p, m);
 }
 
 // lambda at the final step: dJ/d(rho-1) = |u|^2 / 2, dJ/du = rho u, dJ/dPi = 0.

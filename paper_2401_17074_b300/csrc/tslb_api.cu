@@ -171,7 +171,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_INVALID, "unknown precision");
     if (o.precision != TSLB_FP32 && (!(o.u_ref > 0) || !(o.pi_ref > 0)))
         return fail(nullptr, TSLB_ERR_INVALID, "16-bit storage needs positive u_ref and pi_ref");
-    if (o.kernel < TSLB_KERNEL_AUTO || o.kernel > TSLB_KERNEL_FACTORED_TMA)
+    if (o.kernel < TSLB_KERNEL_AUTO || o.kernel > TSLB_KERNEL_FACTORED)
         return fail(nullptr, TSLB_ERR_INVALID, "unknown kernel choice");
     if (o.checkpoint_every < 0) return fail(nullptr, TSLB_ERR_INVALID, "checkpoint_every < 0");
     if (bz0 == TSLB_BC_INFLOW && o.inflow.diameter < 0) return fail(nullptr, TSLB_ERR_INVALID, "bad inflow diameter");
@@ -340,7 +340,7 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (nsteps < 0) return fail(h, TSLB_ERR_INVALID, "nsteps < 0");
     cudaSetDevice(h->device);
-    if ((h->kernel == TSLB_KERNEL_FACTORED || h->kernel == TSLB_KERNEL_FACTORED_TMA) && !tslb::factored_supports(h))
+    if (h->kernel == TSLB_KERNEL_FACTORED && !tslb::factored_supports(h))
         return fail(h, TSLB_ERR_UNSUPPORTED, "the factored kernel does not support this configuration");
     const int k = h->checkpoint_every;
     for (int64_t s = 0; s < nsteps; ++s) {

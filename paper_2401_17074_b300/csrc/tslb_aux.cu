@@ -5,9 +5,8 @@
 namespace tslb {
 namespace {
 
-// Full-lattice FP64 arrays -> interior storage.  Stored quantities are
-// rho - 1, u and Pi^neq; the 16-bit codecs divide u and Pi^neq by their
-// reference scales and round to nearest even.
+// Full-lattice FP64 arrays -> interior storage (layout and 16-bit scaling in
+// NodeIO): rho - 1, u and Pi^neq.
 template <class Codec>
 __global__ void encode_kernel(const double* __restrict__ rho, const double* __restrict__ u,
                               const double* __restrict__ pi, typename Codec::T* __restrict__ dst, Geometry g,
@@ -20,7 +19,7 @@ __global__ void encode_kernel(const double* __restrict__ rho, const double* __re
     v[F_DRHO] = (float)(rho[node] - 1.0);
     for (int a = 0; a < 3; ++a) v[F_UX + a] = (float)u[a * fN + node];
     for (int k = 0; k < 6; ++k) v[F_PXX + k] = pi ? (float)pi[k * fN + node] : 0.0f;
-    for (int f = 0; f < NFIELDS; ++f) dst[f * g.fstride + n] = Codec::enc(v[f], field_inv_scale(f, p));
+    NodeIO<Codec>::store(dst, g.fstride, n, p, v);
 }
 
 // Interior storage -> full-lattice FP64; boundary-layer nodes get the rest state.
@@ -36,7 +35,7 @@ __global__ void decode_kernel(const typename Codec::T* __restrict__ src, double*
     float v[NFIELDS];
     if (inside) {
         const long long n = xi + g.nx * yi + g.plane * zi;
-        for (int f = 0; f < NFIELDS; ++f) v[f] = Codec::dec(src[f * g.fstride + n], field_scale(f, p));
+        NodeIO<Codec>::load(src, g.fstride, n, p, v);
     } else {
         for (int f = 0; f < NFIELDS; ++f) v[f] = 0.0f;
     }
@@ -60,7 +59,7 @@ __global__ void __launch_bounds__(256) diag_partial_kernel(const typename Codec:
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
          n += (long long)gridDim.x * blockDim.x) {
         float v[NFIELDS];
-        for (int f = 0; f < NFIELDS; ++f) v[f] = Codec::dec(src[f * g.fstride + n], field_scale(f, p));
+        NodeIO<Codec>::load(src, g.fstride, n, p, v);
         bool finite = true;
         for (int f = 0; f < NFIELDS; ++f) finite = finite && isfinite(v[f]);
         if (!finite) {

@@ -67,36 +67,140 @@ struct Physics {
     float in_amp;
     unsigned long long in_seed;
     long long t;           // step index of the state being read
-    int* err;              // device status word: nonzero after a bounded wait gave up
+    int* err;              // device status word (nonzero: a kernel gave up a bounded wait)
     // storage scales (16-bit codecs): value = stored * scale
     float s_u, s_pi, inv_s_u, inv_s_pi;
 };
 
-// ---- storage codecs --------------------------------------------------------
+// ---- storage ----------------------------------------------------------------
+// One moment buffer holds three arrays of small vectors, one entry per stored
+// (interior) node, x fastest:
+//     V0 = (rho - 1, u_x, u_y, u_z)        at element 0
+//     V1 = (Pi_xx, Pi_yy, Pi_zz, Pi_xy)    at element 4 * fs
+//     V2 = (Pi_xz, Pi_yz)                  at element 8 * fs
+// (fs = node count padded to 128; 10 * fs elements per buffer).  FP32 storage
+// moves 16 + 16 + 8 bytes per node, 16-bit storage 8 + 8 + 4, each warp access
+// contiguous.  The 16-bit codecs store u / u_ref and Pi / pi_ref (rho - 1
+// unscaled), rounded to nearest even.
 struct CodecF32 {
     typedef float T;
-    static __device__ __forceinline__ float load(const float* p, float) { return __ldg(p); }
-    static __device__ __forceinline__ float dec(float v, float) { return v; }
-    static __device__ __forceinline__ float enc(float v, float) { return v; }
 };
 struct CodecBF16 {
     typedef __nv_bfloat16 T;
-    static __device__ __forceinline__ float dec(T v, float s) { return __bfloat162float(v) * s; }
-    static __device__ __forceinline__ T enc(float v, float inv_s) { return __float2bfloat16_rn(v * inv_s); }
+    typedef __nv_bfloat162 T2;
+    static __device__ __forceinline__ float2 to_f2(T2 v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ T2 from_f2(float a, float b) { return __floats2bfloat162_rn(a, b); }
 };
 struct CodecF16 {
     typedef __half T;
-    static __device__ __forceinline__ float dec(T v, float s) { return __half2float(v) * s; }
-    static __device__ __forceinline__ T enc(float v, float inv_s) { return __float2half_rn(v * inv_s); }
+    typedef __half2 T2;
+    static __device__ __forceinline__ float2 to_f2(T2 v) { return __half22float2(v); }
+    static __device__ __forceinline__ T2 from_f2(float a, float b) { return __floats2half2_rn(a, b); }
 };
 
-// Scale of field f under the 16-bit codecs (drho unscaled).
-__device__ __forceinline__ float field_scale(int f, const Physics& p) {
-    return f == F_DRHO ? 1.0f : (f <= F_UZ ? p.s_u : p.s_pi);
-}
-__device__ __forceinline__ float field_inv_scale(int f, const Physics& p) {
-    return f == F_DRHO ? 1.0f : (f <= F_UZ ? p.inv_s_u : p.inv_s_pi);
-}
+template <class Codec>
+struct NodeIO {
+    typedef typename Codec::T T;
+    typedef typename Codec::T2 T2;
+    static __device__ __forceinline__ float2 unpack(unsigned w) { return Codec::to_f2(*reinterpret_cast<const T2*>(&w)); }
+    static __device__ __forceinline__ unsigned pack(float a, float b) {
+        const T2 v = Codec::from_f2(a, b);
+        return *reinterpret_cast<const unsigned*>(&v);
+    }
+    static __device__ __forceinline__ void load(const T* __restrict__ b, long long fs, long long n, const Physics& p,
+                                                float m[NFIELDS]) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2*>(b) + n);
+        const uint2 c = __ldg(reinterpret_cast<const uint2*>(b + 4 * fs) + n);
+        const unsigned d = __ldg(reinterpret_cast<const unsigned*>(b + 8 * fs) + n);
+        float2 t = unpack(a.x);
+        m[F_DRHO] = t.x;
+        m[F_UX] = t.y * p.s_u;
+        t = unpack(a.y);
+        m[F_UY] = t.x * p.s_u;
+        m[F_UZ] = t.y * p.s_u;
+        t = unpack(c.x);
+        m[F_PXX] = t.x * p.s_pi;
+        m[F_PYY] = t.y * p.s_pi;
+        t = unpack(c.y);
+        m[F_PZZ] = t.x * p.s_pi;
+        m[F_PXY] = t.y * p.s_pi;
+        t = unpack(d);
+        m[F_PXZ] = t.x * p.s_pi;
+        m[F_PYZ] = t.y * p.s_pi;
+    }
+    // Decode one node held as V0 / V1 / V2 vectors at v0, v1, v2 (shared memory).
+    static __device__ __forceinline__ void decode_smem(const T* v0, const T* v1, const T* v2, const Physics& p,
+                                                       float m[NFIELDS]) {
+        const uint2 a = *reinterpret_cast<const uint2*>(v0);
+        const uint2 c = *reinterpret_cast<const uint2*>(v1);
+        const unsigned d = *reinterpret_cast<const unsigned*>(v2);
+        float2 t = unpack(a.x);
+        m[F_DRHO] = t.x;
+        m[F_UX] = t.y * p.s_u;
+        t = unpack(a.y);
+        m[F_UY] = t.x * p.s_u;
+        m[F_UZ] = t.y * p.s_u;
+        t = unpack(c.x);
+        m[F_PXX] = t.x * p.s_pi;
+        m[F_PYY] = t.y * p.s_pi;
+        t = unpack(c.y);
+        m[F_PZZ] = t.x * p.s_pi;
+        m[F_PXY] = t.y * p.s_pi;
+        t = unpack(d);
+        m[F_PXZ] = t.x * p.s_pi;
+        m[F_PYZ] = t.y * p.s_pi;
+    }
+    static __device__ __forceinline__ void store(T* __restrict__ b, long long fs, long long n, const Physics& p,
+                                                 const float m[NFIELDS]) {
+        const float iu = p.inv_s_u, ip = p.inv_s_pi;
+        reinterpret_cast<uint2*>(b)[n] = make_uint2(pack(m[F_DRHO], m[F_UX] * iu), pack(m[F_UY] * iu, m[F_UZ] * iu));
+        reinterpret_cast<uint2*>(b + 4 * fs)[n] =
+            make_uint2(pack(m[F_PXX] * ip, m[F_PYY] * ip), pack(m[F_PZZ] * ip, m[F_PXY] * ip));
+        reinterpret_cast<unsigned*>(b + 8 * fs)[n] = pack(m[F_PXZ] * ip, m[F_PYZ] * ip);
+    }
+};
+
+template <>
+struct NodeIO<CodecF32> {
+    static __device__ __forceinline__ void load(const float* __restrict__ b, long long fs, long long n, const Physics&,
+                                                float m[NFIELDS]) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(b) + n);
+        const float4 c = __ldg(reinterpret_cast<const float4*>(b + 4 * fs) + n);
+        const float2 d = __ldg(reinterpret_cast<const float2*>(b + 8 * fs) + n);
+        m[F_DRHO] = a.x;
+        m[F_UX] = a.y;
+        m[F_UY] = a.z;
+        m[F_UZ] = a.w;
+        m[F_PXX] = c.x;
+        m[F_PYY] = c.y;
+        m[F_PZZ] = c.z;
+        m[F_PXY] = c.w;
+        m[F_PXZ] = d.x;
+        m[F_PYZ] = d.y;
+    }
+    static __device__ __forceinline__ void decode_smem(const float* v0, const float* v1, const float* v2,
+                                                       const Physics&, float m[NFIELDS]) {
+        const float4 a = *reinterpret_cast<const float4*>(v0);
+        const float4 c = *reinterpret_cast<const float4*>(v1);
+        const float2 d = *reinterpret_cast<const float2*>(v2);
+        m[F_DRHO] = a.x;
+        m[F_UX] = a.y;
+        m[F_UY] = a.z;
+        m[F_UZ] = a.w;
+        m[F_PXX] = c.x;
+        m[F_PYY] = c.y;
+        m[F_PZZ] = c.z;
+        m[F_PXY] = c.w;
+        m[F_PXZ] = d.x;
+        m[F_PYZ] = d.y;
+    }
+    static __device__ __forceinline__ void store(float* __restrict__ b, long long fs, long long n, const Physics&,
+                                                 const float m[NFIELDS]) {
+        reinterpret_cast<float4*>(b)[n] = make_float4(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ]);
+        reinterpret_cast<float4*>(b + 4 * fs)[n] = make_float4(m[F_PXX], m[F_PYY], m[F_PZZ], m[F_PXY]);
+        reinterpret_cast<float2*>(b + 8 * fs)[n] = make_float2(m[F_PXZ], m[F_PYZ]);
+    }
+};
 
 // ---- Hermite algebra -------------------------------------------------------
 constexpr float CS2 = 1.0f / 3.0f;
@@ -265,7 +369,6 @@ cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, co
 // The step kernel tslb_step uses for this handle (same choice, bitwise-identical results).
 cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p);
 bool use_factored(const tslb_s* h);
-bool factored_uses_tma(const tslb_s* h);
 int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, std::string* msg);
 bool factored_supports(const tslb_s* h);
 cudaError_t launch_encode(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst,

@@ -17,8 +17,7 @@ namespace {
 template <class Codec>
 __device__ __forceinline__ void load_node(const typename Codec::T* __restrict__ src, const Geometry& g,
                                           const Physics& p, long long idx, float m[NFIELDS]) {
-#pragma unroll
-    for (int f = 0; f < NFIELDS; ++f) m[f] = Codec::dec(src[f * g.fstride + idx], field_scale(f, p));
+    NodeIO<Codec>::load(src, g.fstride, idx, p, m);
 }
 
 template <class Codec>
@@ -108,8 +107,7 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
     // New moments (Sec. 2.1) from the 216-scaled deviation sums.
     float out[NFIELDS];
     finish_moments(D0, J, S, out);
-#pragma unroll
-    for (int f = 0; f < NFIELDS; ++f) dst[f * g.fstride + n] = Codec::enc(out[f], field_inv_scale(f, p));
+    NodeIO<Codec>::store(dst, g.fstride, n, p, out);
 }
 
 }  // namespace

@@ -18,20 +18,15 @@
 // marches z, so z-neighbours are the previous / next loop iterations), then y
 // through shared memory (warps are rows), then x through warp shuffles
 // (lanes are columns).  Halo: lanes 0 and 31 and the first and last warp
-// recompute the border columns / rows of the tile.
+// recompute the border columns / rows of the tile.  The z pass starts from
+// the unscaled Hermite coefficients with the mode scale factors folded into
+// its fused multiply-adds.
 //
-// Memory path (default): each thread loads the 10 moments of its column with
-// coalesced per-thread global loads, one plane ahead of the plane it is
-// processing (register prefetch); stores go straight to global memory.
-// Optional TMA feed (TSLB_KERNEL_FACTORED_TMA, when the row pitch is a multiple
-// of 16 bytes): the plane tiles (+ halo) come into a three-stage shared-memory
-// ring by cp.async.bulk.tensor, one box per field issued by the lanes of the
-// last warp, completion counted on an mbarrier per stage; periodic wrap-around
-// columns / rows come from small extra boxes in side regions that share the
-// field stride, so only a thread's base offset depends on where its column
-// lives.  On the B300 the register-prefetch feed measured faster (36.3 vs 29.1
-// GLUPS on the 512 x 130 x 256 channel): the 217 KB ring leaves little L1 for
-// the halo re-reads and every warp waits for a whole plane.
+// Memory path: each thread copies its column's moments one plane ahead into
+// its own shared-memory slots (three cp.async vector copies, L1-cached so the
+// halo re-reads of neighbouring tiles hit), reads them back when the plane
+// comes up, and stores its node's new moments with three vector stores; the
+// y exchange moves four values per shared-memory access.
 //
 // Faces: periodic axes wrap; a free-slip face mirrors the 1-D pass (the
 // population entering from the wall side is the node's own population leaving
@@ -40,10 +35,7 @@
 // bounce-back); inflow / outflow z faces enter the march as ghost planes
 // (Eq. neq_final for the inflow, the adjacent layer's moments for the
 // outflow, Sec. 3.2).
-#include <cuda.h>
-
 #include <algorithm>
-#include <mutex>
 
 #include "tslb_internal.cuh"
 
@@ -54,92 +46,42 @@ constexpr int XOUT = 30;   // output columns per warp (lanes 1..30)
 constexpr int WROWS = 18;  // warps per CTA; rows 1..16 are outputs
 constexpr int YOUT = WROWS - 2;
 constexpr int NT = 32 * WROWS;
-constexpr int YSLOTS = 18;  // y-exchange values per thread: 9 groups x {p+, p-}
-constexpr int NSTAGE = 3;   // TMA ring depth (planes)
-constexpr size_t YBYTES = sizeof(float) * 2 * YSLOTS * NT;
+// y exchange per thread and buffer: p+ of groups 0-7 (two float4), p- of
+// groups 0-7 (two float4), then p+ and p- of group 8 (two floats)
+constexpr int YV = 4;  // float4 slots
+constexpr int YS = 2;  // float slots
+constexpr size_t YBUF = sizeof(float) * (4 * YV + YS) * NT;
 
-constexpr int align128(int b) { return (b + 127) / 128 * 128; }
-
-// Shared-memory layout of one field of one stage, for element size E.
+// Plane prefetch: every thread copies its column's next-plane moments into its
+// own shared-memory slots with cp.async (L1-cached, no registers held while
+// the copy is in flight), double-buffered.  Slot regions per buffer: V0, V1
+// (16 bytes per thread at FP32, 8 at 16-bit) and V2 (8 / 4 bytes).
 template <int E>
-struct StageLayout {
-    static constexpr int BX = E == 4 ? 36 : 40;  // main box width (covers 32 columns + alignment shift)
-    static constexpr int XW = 16 / E;            // width of a wrap box (16 bytes)
-    static constexpr int MAIN = 0;
-    static constexpr int XL = MAIN + align128(WROWS * BX * E);
-    static constexpr int XR = XL + align128(WROWS * XW * E);
-    static constexpr int YB = XR + align128(WROWS * XW * E);
-    static constexpr int YT = YB + align128(BX * E);
-    static constexpr int CLB = YT + align128(BX * E);
-    static constexpr int CRB = CLB + 128;
-    static constexpr int CLT = CRB + 128;
-    static constexpr int CRT = CLT + 128;
-    static constexpr int FIELD = CRT + 128;  // bytes per field
-    static constexpr int STAGE = NFIELDS * FIELD;
-    static constexpr size_t SMEM = 128 + YBYTES + (size_t)NSTAGE * STAGE;
+struct Prefetch {
+    static constexpr int B01 = 4 * E;  // bytes per thread of V0 and of V1
+    static constexpr int B2 = 2 * E;   // bytes per thread of V2
+    static constexpr size_t BUF = (size_t)(2 * B01 + B2) * NT;
 };
+template <int E>
+constexpr size_t smem_bytes() { return 2 * YBUF + 2 * Prefetch<E>::BUF; }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// 1-D populations of a pass: p+, p- and c = a0 - a2 (p0 = 4 c).
 struct Pops {
     float pp, pm, c;
 };
 __device__ __forceinline__ Pops pops3(float a0, float a1, float a2) {
     const float e = fmaf(2.0f, a2, a0);
-    return {e + a1, e - a1, 4.0f * (a0 - a2)};
+    return {e + a1, e - a1, a0 - a2};
 }
-__device__ __forceinline__ Pops pops2(float a0, float a1) { return {a0 + a1, a0 - a1, 4.0f * a0}; }
-__device__ __forceinline__ Pops pops1(float a0) { return {a0, a0, 4.0f * a0}; }
-
-// ---- PTX helpers: mbarrier + TMA ------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: gives up after about two seconds of SM clock.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > 4000000000LL) return false;
-    return true;
-}
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
-                                            int c2, int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
-// Tensor maps of one moment buffer: [field][z][y][x] viewed as a 4-D tensor
-// (x, y, z, field); boxes main {BX, 18}, column wrap {XW, 18}, row wrap
-// {BX, 1}, corner {XW, 1}, all one plane and one field deep.
-struct TmaMaps {
-    CUtensorMap main, col, row, corner;
-};
-
-// Moments of one node from global memory; `off` is the node's offset inside a field.
-template <class Codec>
-__device__ __forceinline__ void load_moments(const typename Codec::T* __restrict__ src, long long fstride,
-                                             unsigned off, const Physics& p, float m[NFIELDS]) {
-#pragma unroll
-    for (int f = 0; f < NFIELDS; ++f) m[f] = Codec::dec(src[f * fstride + off], field_scale(f, p));
-}
+__device__ __forceinline__ Pops pops2(float a0, float a1) { return {a0 + a1, a0 - a1, a0}; }
 
 // Interior plane stored at march position zs (periodic wrap, inflow / outflow ghosts).
 __device__ __forceinline__ int plane_of(int zs, const Geometry& g, bool zper, bool& inflow_ghost) {
@@ -153,92 +95,136 @@ __device__ __forceinline__ int plane_of(int zs, const Geometry& g, bool zper, bo
     return zs;
 }
 
+// Unscaled Hermite coefficients of the post-collision population (see
+// post_modes): rho - 1, j = rho (u + F), h2, h3 with P = (1 - omega) Pi;
+// (u, F) enter the equilibrium part, (v, Pi) the non-equilibrium part.
+struct Herm {
+    float drho, jx, jy, jz, xx, yy, zz, xy, xz, yz, xxy, xxz, xyy, yyz, xzz, yzz, xyz;
+};
+__device__ __forceinline__ Herm hermite(float drho, float ux, float uy, float uz, float vx, float vy, float vz,
+                                        const float pi[6], float Fx, float Fy, float Fz, float omega1) {
+    Herm h;
+    const float rho = 1.0f + drho;
+    const float pxx = omega1 * pi[0], pyy = omega1 * pi[1], pzz = omega1 * pi[2];
+    const float pxy = omega1 * pi[3], pxz = omega1 * pi[4], pyz = omega1 * pi[5];
+    const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
+    h.drho = drho;
+    h.jx = fmaf(rho, Fx, rux);
+    h.jy = fmaf(rho, Fy, ruy);
+    h.jz = fmaf(rho, Fz, ruz);
+    h.xx = fmaf(rux, ux, pxx);
+    h.yy = fmaf(ruy, uy, pyy);
+    h.zz = fmaf(ruz, uz, pzz);
+    const float qxy = rux * uy, qxz = rux * uz, qyz = ruy * uz;
+    h.xy = qxy + pxy;
+    h.xz = qxz + pxz;
+    h.yz = qyz + pyz;
+    h.xxy = fmaf(qxy, ux, fmaf(2.0f * vx, pxy, vy * pxx));
+    h.xxz = fmaf(qxz, ux, fmaf(2.0f * vx, pxz, vz * pxx));
+    h.xyy = fmaf(qxy, uy, fmaf(2.0f * vy, pxy, vx * pyy));
+    h.yyz = fmaf(qyz, uy, fmaf(2.0f * vy, pyz, vz * pyy));
+    h.xzz = fmaf(qxz, uz, fmaf(2.0f * vz, pxz, vx * pzz));
+    h.yzz = fmaf(qyz, uz, fmaf(2.0f * vz, pyz, vy * pzz));
+    h.xyz = fmaf(qxy, uz, fmaf(vx, pyz, fmaf(vy, pxz, vz * pxy)));
+    return h;
+}
+
+// z populations of the eight (k1, k2) groups, modes
+//   (000, 001, 002) = (drho, 3 j_z, 1.5 h_zz),  (100, 101, 102) = (3 j_x, 9 h_xz, 4.5 h_xzz),
+//   (010, 011, 012) = (3 j_y, 9 h_yz, 4.5 h_yzz), (200, 201) = (1.5 h_xx, 4.5 h_xxz),
+//   (020, 021) = (1.5 h_yy, 4.5 h_yyz), (110, 111) = (9 h_xy, 27 h_xyz), 210 = 4.5 h_xxy,
+//   120 = 4.5 h_xyy, with the scale factors folded into the multiply-adds.
+__device__ __forceinline__ void zpops(const Herm& h, Pops P[8]) {
+    {
+        const float e = fmaf(3.0f, h.zz, h.drho);
+        P[0] = {fmaf(3.0f, h.jz, e), fmaf(-3.0f, h.jz, e), fmaf(-1.5f, h.zz, h.drho)};
+    }
+    {
+        const float t = 3.0f * h.jx, e = fmaf(9.0f, h.xzz, t);
+        P[1] = {fmaf(9.0f, h.xz, e), fmaf(-9.0f, h.xz, e), fmaf(-4.5f, h.xzz, t)};
+    }
+    {
+        const float t = 3.0f * h.jy, e = fmaf(9.0f, h.yzz, t);
+        P[2] = {fmaf(9.0f, h.yz, e), fmaf(-9.0f, h.yz, e), fmaf(-4.5f, h.yzz, t)};
+    }
+    {
+        const float t = 1.5f * h.xx;
+        P[3] = {fmaf(4.5f, h.xxz, t), fmaf(-4.5f, h.xxz, t), t};
+    }
+    {
+        const float t = 1.5f * h.yy;
+        P[4] = {fmaf(4.5f, h.yyz, t), fmaf(-4.5f, h.yyz, t), t};
+    }
+    {
+        const float t = 9.0f * h.xy;
+        P[5] = {fmaf(27.0f, h.xyz, t), fmaf(-27.0f, h.xyz, t), t};
+    }
+    {
+        const float t = 4.5f * h.xxy;
+        P[6] = {t, t, t};
+    }
+    {
+        const float t = 4.5f * h.xyy;
+        P[7] = {t, t, t};
+    }
+}
+
 // Per-thread constants of the march.
 struct Ctx {
     int tid, lane, warp, x, y, xl, yl;
     unsigned col, plane;
     int z0, z1, np;  // march covers planes z0-1 .. z1 (np of them)
     bool zper, ybb, store, row_lo, row_hi, zero_row, xlo_mirror, xhi_mirror;
-    int offL, offR;      // y-exchange read offsets (relative to a slot base)
-    uint32_t roff;       // byte offset of this thread's value inside a stage field (TMA path)
-    uint32_t tx_bytes;   // bytes expected per stage fill (TMA path)
-    bool xl_wrap, xr_wrap, yb_wrap, yt_wrap;
-    int xa;              // first column of the main TMA box
-    int issued;          // planes whose TMA fill has been issued (thread 0)
+    int offLv, offRv, offLs, offRs;  // y-exchange read offsets (float4 / float units, relative to a slot base)
 };
 
-template <class Codec, bool XFREE, bool TMA>
+template <class Codec, bool XFREE>
 struct Kernel {
     typedef typename Codec::T T;
-    typedef StageLayout<(int)sizeof(T)> SL;
-
-    // Issue the TMA boxes of march plane j into its stage.  Called by the
-    // whole last warp: lane f issues the boxes of field f, so the ten fields go
-    // out in one warp instruction instead of a serial loop on one thread.
-    static __device__ __forceinline__ void fill(const Ctx& c, const Geometry& g, const TmaMaps& tm, char* stages,
-                                                uint32_t bars, int j) {
-        const int zs = c.z0 - 1 + j;
-        bool ig;
-        const int zl = plane_of(zs, g, c.zper, ig);
-        const int s = j % NSTAGE;
-        const uint32_t bar = bars + 8u * s;
-        const uint32_t base = smem_u32(stages + (size_t)s * SL::STAGE);
-        if (c.lane == 0) mbar_expect_tx(bar, c.tx_bytes);
-        __syncwarp();
-        const int y0m = (int)blockIdx.y * YOUT - 1;
-        const int f = c.lane;
-        if (f < NFIELDS) {
-            const uint32_t fb = base + f * SL::FIELD;
-            tma_load_4d(fb + SL::MAIN, &tm.main, bar, c.xa, y0m, zl, f);
-            if (c.xl_wrap) tma_load_4d(fb + SL::XL, &tm.col, bar, g.nx - SL::XW, y0m, zl, f);
-            if (c.xr_wrap) tma_load_4d(fb + SL::XR, &tm.col, bar, 0, y0m, zl, f);
-            if (c.yb_wrap) tma_load_4d(fb + SL::YB, &tm.row, bar, c.xa, g.ny - 1, zl, f);
-            if (c.yt_wrap) tma_load_4d(fb + SL::YT, &tm.row, bar, c.xa, 0, zl, f);
-            if (c.xl_wrap && c.yb_wrap) tma_load_4d(fb + SL::CLB, &tm.corner, bar, g.nx - SL::XW, g.ny - 1, zl, f);
-            if (c.xr_wrap && c.yb_wrap) tma_load_4d(fb + SL::CRB, &tm.corner, bar, 0, g.ny - 1, zl, f);
-            if (c.xl_wrap && c.yt_wrap) tma_load_4d(fb + SL::CLT, &tm.corner, bar, g.nx - SL::XW, 0, zl, f);
-            if (c.xr_wrap && c.yt_wrap) tma_load_4d(fb + SL::CRT, &tm.corner, bar, 0, 0, zl, f);
-        }
-    }
 
     // One march position j (plane zs = z0 - 1 + j).  ppOld holds p+ of plane
-    // zs-2 on entry and p+ of plane zs on exit; cOld holds p0 of zs-1; cNew
-    // receives p0 of zs.
-    // Returns true (uniformly across the CTA) when a bounded wait gave up.
-    static __device__ __forceinline__ bool plane_step(Ctx& c, const Geometry& g, const Physics& p,
-                                                      const T* __restrict__ src, T* __restrict__ dst,
-                                                      const TmaMaps& tm, char* stages, uint32_t bars, float* ysm,
-                                                      float (&mn)[NFIELDS], int j, float (&ppOld)[8],
-                                                      const float (&cOld)[8], float (&cNew)[8]) {
-        int timed_out = 0;
+    // zs-2 on entry and p+ of plane zs on exit; cOld holds c of zs-1; cNew
+    // receives c of zs.
+    typedef Prefetch<(int)sizeof(T)> PF;
+
+    // Start the copies of march plane j's moments into prefetch buffer j & 1.
+    static __device__ __forceinline__ void prefetch(const Ctx& c, const Geometry& g, const T* __restrict__ src,
+                                                    char* pfb, int j) {
+        bool ig;
+        const int zl = plane_of(c.z0 - 1 + j, g, c.zper, ig);
+        const unsigned n = c.col + c.plane * (unsigned)zl;
+        char* b = pfb + (j & 1) * PF::BUF;
+        cp_async<PF::B01>(smem_u32(b + c.tid * PF::B01), src + (size_t)n * 4);
+        cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * g.fstride + (size_t)n * 4);
+        cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * g.fstride + (size_t)n * 2);
+        cp_async_commit();
+    }
+
+    static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
+                                                      const T* __restrict__ src, T* __restrict__ dst, float* ysm,
+                                                      char* pfb, int j, float (&ppOld)[8], const float (&cOld)[8],
+                                                      float (&cNew)[8]) {
         const int zs = c.z0 - 1 + j;
         bool inflow_ghost;
         const int zl = plane_of(zs, g, c.zper, inflow_ghost);
         const unsigned idx = c.col + c.plane * (unsigned)zl;
+        // next plane's copies go out before this plane's are consumed
+        if (zs < c.z1) prefetch(c, g, src, pfb, j + 1);
+        else cp_async_commit();
+        cp_async_wait_prev();
         float m[NFIELDS];
-        if constexpr (TMA) {
-            const int s = j % NSTAGE;
-            if (!mbar_wait(bars + 8u * s, (uint32_t)((j / NSTAGE) & 1))) {
-                timed_out = 1;
-                if (p.err) atomicExch(p.err, 1);
-            }
-            const T* rp = reinterpret_cast<const T*>(stages + (size_t)s * SL::STAGE + c.roff);
-#pragma unroll
-            for (int f = 0; f < NFIELDS; ++f) m[f] = Codec::dec(rp[f * (SL::FIELD / (int)sizeof(T))], field_scale(f, p));
-        } else {
-#pragma unroll
-            for (int f = 0; f < NFIELDS; ++f) m[f] = mn[f];
-            if (zs < c.z1) {
-                bool ig;
-                const int zn = plane_of(zs + 1, g, c.zper, ig);
-                load_moments<Codec>(src, g.fstride, c.col + c.plane * (unsigned)zn, p, mn);
-            }
+        {
+            const char* b = pfb + (j & 1) * PF::BUF;
+            const T* v0 = reinterpret_cast<const T*>(b + c.tid * PF::B01);
+            const T* v1 = reinterpret_cast<const T*>(b + NT * PF::B01 + c.tid * PF::B01);
+            const T* v2 = reinterpret_cast<const T*>(b + 2 * NT * PF::B01 + c.tid * PF::B2);
+            NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
         }
-        // ---- source plane: moments -> 17 modes -> z populations --------------
-        float A[NMODES];
+        // ---- source plane: moments -> Hermite coefficients -> z populations ----
+        Herm h;
         if (inflow_ghost) {
             const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
-            post_modes(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f, p.omega1, A);
+            h = hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f, p.omega1);
         } else {
             float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
             if (p.force) {
@@ -246,18 +232,11 @@ struct Kernel {
                 F1 = __ldg(p.force + g.fstride + idx);
                 F2 = __ldg(p.force + 2 * g.fstride + idx);
             }
-            post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
-                       p.omega1, A);
+            h = hermite(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
+                        p.omega1);
         }
         Pops P[8];
-        P[0] = pops3(A[M000], A[M001], A[M002]);  // (k1,k2) = (0,0)
-        P[1] = pops3(A[M100], A[M101], A[M102]);  // (1,0)
-        P[2] = pops3(A[M010], A[M011], A[M012]);  // (0,1)
-        P[3] = pops2(A[M200], A[M201]);           // (2,0)
-        P[4] = pops2(A[M020], A[M021]);           // (0,2)
-        P[5] = pops2(A[M110], A[M111]);           // (1,1)
-        P[6] = pops1(A[M210]);                    // (2,1)
-        P[7] = pops1(A[M120]);                    // (1,2)
+        zpops(h, P);
 
         if (zs >= c.z0 + 1) {
             // ---- z moments of plane z = zs - 1 ------------------------------
@@ -267,9 +246,9 @@ struct Kernel {
                 const float L = ppOld[k], R = P[k].pm;
                 Z[k][2] = L + R;
                 Z[k][1] = L - R;
-                Z[k][0] = Z[k][2] + cOld[k];
+                Z[k][0] = fmaf(4.0f, cOld[k], Z[k][2]);
             }
-            // ---- y pass: groups (k1, r) over k2 -----------------------------
+            // ---- y pass: groups jj = 3 k1 + r over k2 -----------------------
             Pops Q[9];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -277,19 +256,36 @@ struct Kernel {
                 Q[3 + r] = pops3(Z[1][r], Z[5][r], Z[7][r]);  // k1 = 1
                 Q[6 + r] = pops2(Z[3][r], Z[6][r]);           // k1 = 2
             }
-            float* sb = ysm + (j & 1) * (YSLOTS * NT);
+            float* sb = ysm + (j & 1) * (YBUF / sizeof(float));
+            float4* sv = reinterpret_cast<float4*>(sb);
+            float* ss = sb + 4 * YV * NT;
             if (c.zero_row) {
                 // ghost row beyond a bounce-back wall: the entering deviation is zero
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int q = 0; q < 2 * 9; ++q) sb[q * NT + c.tid] = 0.0f;
+                for (int q = 0; q < YV; ++q) sv[q * NT + c.tid] = z4;
+                ss[c.tid] = 0.0f;
+                ss[NT + c.tid] = 0.0f;
             } else {
-#pragma unroll
-                for (int jj = 0; jj < 9; ++jj) {
-                    sb[(2 * jj) * NT + c.tid] = Q[jj].pp;
-                    sb[(2 * jj + 1) * NT + c.tid] = Q[jj].pm;
-                }
+                sv[0 * NT + c.tid] = make_float4(Q[0].pp, Q[1].pp, Q[2].pp, Q[3].pp);
+                sv[1 * NT + c.tid] = make_float4(Q[4].pp, Q[5].pp, Q[6].pp, Q[7].pp);
+                sv[2 * NT + c.tid] = make_float4(Q[0].pm, Q[1].pm, Q[2].pm, Q[3].pm);
+                sv[3 * NT + c.tid] = make_float4(Q[4].pm, Q[5].pm, Q[6].pm, Q[7].pm);
+                ss[c.tid] = Q[8].pp;
+                ss[NT + c.tid] = Q[8].pm;
             }
-            timed_out = __syncthreads_or(timed_out);
+            __syncthreads();
+            float L[9], R[9];
+            {
+                const float4 l0 = sv[0 * NT + c.offLv], l1 = sv[1 * NT + c.offLv];
+                const float4 r0 = sv[2 * NT + c.offRv], r1 = sv[3 * NT + c.offRv];
+                L[0] = l0.x; L[1] = l0.y; L[2] = l0.z; L[3] = l0.w;
+                L[4] = l1.x; L[5] = l1.y; L[6] = l1.z; L[7] = l1.w;
+                R[0] = r0.x; R[1] = r0.y; R[2] = r0.z; R[3] = r0.w;
+                R[4] = r1.x; R[5] = r1.y; R[6] = r1.z; R[7] = r1.w;
+                L[8] = ss[c.offLs];
+                R[8] = ss[NT + c.offRs];
+            }
             // Y[k1][q][r] for (q, r) in {(0,0),(1,0),(2,0),(0,1),(1,1),(0,2)}
             float Y[3][6];
 #pragma unroll
@@ -297,18 +293,16 @@ struct Kernel {
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
                     const int jj = 3 * k1 + r;
-                    const float L = sb[(2 * jj) * NT + c.offL];
-                    const float R = sb[(2 * jj + 1) * NT + c.offR];
-                    const float sLR = L + R;
+                    const float sLR = L[jj] + R[jj];
                     if (r == 0) {
-                        Y[k1][0] = sLR + Q[jj].c;  // q = 0
-                        Y[k1][1] = L - R;          // q = 1
-                        Y[k1][2] = sLR;            // q = 2
+                        Y[k1][0] = fmaf(4.0f, Q[jj].c, sLR);  // q = 0
+                        Y[k1][1] = L[jj] - R[jj];              // q = 1
+                        Y[k1][2] = sLR;                        // q = 2
                     } else if (r == 1) {
-                        Y[k1][3] = sLR + Q[jj].c;  // (q, r) = (0, 1)
-                        Y[k1][4] = L - R;          // (1, 1)
+                        Y[k1][3] = fmaf(4.0f, Q[jj].c, sLR);  // (q, r) = (0, 1)
+                        Y[k1][4] = L[jj] - R[jj];              // (1, 1)
                     } else {
-                        Y[k1][5] = sLR + Q[jj].c;  // (0, 2)
+                        Y[k1][5] = fmaf(4.0f, Q[jj].c, sLR);  // (0, 2)
                     }
                 }
             }
@@ -317,15 +311,15 @@ struct Kernel {
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const Pops X = pops3(Y[0][k], Y[1][k], Y[2][k]);
-                float L = __shfl_up_sync(0xffffffffu, X.pp, 1);
-                float R = __shfl_down_sync(0xffffffffu, X.pm, 1);
+                float Lx = __shfl_up_sync(0xffffffffu, X.pp, 1);
+                float Rx = __shfl_down_sync(0xffffffffu, X.pm, 1);
                 if (XFREE) {
-                    if (c.xlo_mirror) L = X.pm;
-                    if (c.xhi_mirror) R = X.pp;
+                    if (c.xlo_mirror) Lx = X.pm;
+                    if (c.xhi_mirror) Rx = X.pp;
                 }
-                const float sLR = L + R;
-                Mo[k][0] = sLR + X.c;
-                Mo[k][1] = L - R;
+                const float sLR = Lx + Rx;
+                Mo[k][0] = fmaf(4.0f, X.c, sLR);
+                Mo[k][1] = Lx - Rx;
                 Mo[k][2] = sLR;
             }
             float D0 = Mo[0][0];
@@ -336,7 +330,7 @@ struct Kernel {
             // ---- halfway bounce-back on the wall-adjacent rows --------------
             if (c.ybb && (c.row_lo || c.row_hi)) {
                 float mo[NFIELDS];
-                load_moments<Codec>(src, g.fstride, oidx, p, mo);
+                NodeIO<Codec>::load(src, g.fstride, oidx, p, mo);
                 float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
                 if (p.force) {
                     F0 = __ldg(p.force + oidx);
@@ -366,20 +360,7 @@ struct Kernel {
             }
             float out[NFIELDS];
             finish_moments(D0, J, S, out);
-            if (c.store) {
-#pragma unroll
-                for (int f = 0; f < NFIELDS; ++f) dst[f * g.fstride + oidx] = Codec::enc(out[f], field_inv_scale(f, p));
-            }
-        } else {
-            timed_out = __syncthreads_or(timed_out);
-        }
-        // every thread has read plane zs: its stage can take plane zs + NSTAGE
-        if constexpr (TMA) {
-            if (!timed_out && c.warp == WROWS - 1 && j + NSTAGE < c.np) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                fill(c, g, tm, stages, bars, j + NSTAGE);
-                c.issued = j + NSTAGE + 1;
-            }
+            if (c.store) NodeIO<Codec>::store(dst, g.fstride, oidx, p, out);
         }
         // ---- advance the z window --------------------------------------------
 #pragma unroll
@@ -387,21 +368,16 @@ struct Kernel {
             ppOld[k] = P[k].pp;
             cNew[k] = P[k].c;
         }
-        return timed_out != 0;
     }
 };
 
-template <class Codec, bool XFREE, bool TMA>
+template <class Codec, bool XFREE>
 __global__ void __launch_bounds__(NT, 1)
     step_factored_kernel(const typename Codec::T* __restrict__ src, typename Codec::T* __restrict__ dst, Geometry g,
-                         Physics p, int zchunk, const __grid_constant__ TmaMaps tm) {
-    typedef Kernel<Codec, XFREE, TMA> K;
-    typedef typename K::SL SL;
-    extern __shared__ __align__(128) char smem[];
-    uint64_t* barp = reinterpret_cast<uint64_t*>(smem);         // [NSTAGE] mbarriers (128-byte header)
-    float* ysm = reinterpret_cast<float*>(smem + 128);          // [2][YSLOTS][NT]
-    char* stages = smem + 128 + YBYTES;                         // [NSTAGE][NFIELDS][FIELD]
-    const uint32_t bars = smem_u32(barp);
+                         Physics p, int zchunk) {
+    typedef Kernel<Codec, XFREE> K;
+    extern __shared__ __align__(16) float ysm[];  // [2][YBUF] y exchange, then [2][PF::BUF] plane prefetch
+    char* pfb = reinterpret_cast<char*>(ysm) + 2 * YBUF;
 
     Ctx c;
     c.tid = threadIdx.x;
@@ -410,7 +386,6 @@ __global__ void __launch_bounds__(NT, 1)
     const int x0 = (int)blockIdx.x * XOUT, y0 = (int)blockIdx.y * YOUT;
     c.x = x0 + c.lane - 1;
     c.y = y0 + c.warp - 1;
-    const bool xper = !XFREE;
     const bool yper = g.bc[2] == TSLB_BC_PERIODIC;
     c.ybb = g.bc[2] == TSLB_BC_BOUNCEBACK;
     const bool yfs = g.bc[2] == TSLB_BC_FREESLIP;
@@ -425,161 +400,42 @@ __global__ void __launch_bounds__(NT, 1)
     c.row_lo = c.y == 0;
     c.row_hi = c.y == g.ny - 1;
     c.zero_row = c.ybb && (c.y == -1 || c.y == g.ny);
-    // y-exchange read offsets: the row below / above, or the node's own value
-    // of the opposite population on a free-slip wall row
-    c.offL = (yfs && c.row_lo) ? NT + c.tid : (c.warp > 0 ? c.tid - 32 : c.tid);
-    c.offR = (yfs && c.row_hi) ? c.tid - NT : (c.warp < WROWS - 1 ? c.tid + 32 : c.tid);
+    // y-exchange read offsets: the row below / above, or -- on a free-slip wall
+    // row -- the node's own value of the opposite population (p- slots sit
+    // 2 float4 slots after the p+ slots, the scalar p- one float slot after p+)
+    const int below = c.warp > 0 ? c.tid - 32 : c.tid, above = c.warp < WROWS - 1 ? c.tid + 32 : c.tid;
+    c.offLv = (yfs && c.row_lo) ? 2 * NT + c.tid : below;
+    c.offRv = (yfs && c.row_hi) ? c.tid - 2 * NT : above;
+    c.offLs = (yfs && c.row_lo) ? NT + c.tid : below;
+    c.offRs = (yfs && c.row_hi) ? c.tid - NT : above;
     c.z0 = (int)blockIdx.z * zchunk;
     c.z1 = min(c.z0 + zchunk, g.nz);
     c.np = c.z1 - c.z0 + 2;
 
-    float mn[NFIELDS];
-    if constexpr (TMA) {
-        constexpr int E = (int)sizeof(typename Codec::T);
-        c.xa = (x0 - 1) & ~(SL::XW - 1);
-        c.xl_wrap = xper && x0 == 0;
-        c.xr_wrap = xper && x0 - 1 <= g.nx && g.nx <= x0 + XOUT;
-        c.yb_wrap = yper && y0 == 0;
-        c.yt_wrap = yper && y0 - 1 <= g.ny && g.ny <= y0 + YOUT;
-        uint32_t per_field = WROWS * SL::BX;
-        if (c.xl_wrap) per_field += WROWS * SL::XW;
-        if (c.xr_wrap) per_field += WROWS * SL::XW;
-        if (c.yb_wrap) per_field += SL::BX;
-        if (c.yt_wrap) per_field += SL::BX;
-        if (c.xl_wrap && c.yb_wrap) per_field += SL::XW;
-        if (c.xr_wrap && c.yb_wrap) per_field += SL::XW;
-        if (c.xl_wrap && c.yt_wrap) per_field += SL::XW;
-        if (c.xr_wrap && c.yt_wrap) per_field += SL::XW;
-        c.tx_bytes = per_field * NFIELDS * E;
-        // where this thread's column lives inside a stage field
-        const bool wl = xper && c.x == -1, wr = xper && c.x == g.nx;
-        const bool wb = yper && c.y == -1, wt = yper && c.y == g.ny;
-        const int row = c.warp, cx = c.x - c.xa;
-        int off;
-        if (wl && wb) off = SL::CLB + (SL::XW - 1) * E;
-        else if (wr && wb) off = SL::CRB;
-        else if (wl && wt) off = SL::CLT + (SL::XW - 1) * E;
-        else if (wr && wt) off = SL::CRT;
-        else if (wl) off = SL::XL + (row * SL::XW + SL::XW - 1) * E;
-        else if (wr) off = SL::XR + (row * SL::XW) * E;
-        else if (wb) off = SL::YB + cx * E;
-        else if (wt) off = SL::YT + cx * E;
-        else off = SL::MAIN + (row * SL::BX + cx) * E;
-        c.roff = (uint32_t)off;
-        if (c.tid == 0) {
-            for (int s = 0; s < NSTAGE; ++s) mbar_init(bars + 8u * s, 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
-        c.issued = 0;
-        if (c.warp == WROWS - 1)
-            for (int j = 0; j < NSTAGE && j < c.np; ++j) {
-                K::fill(c, g, tm, stages, bars, j);
-                c.issued = j + 1;
-            }
-    } else {
-        bool ig;
-        const int zl = plane_of(c.z0 - 1, g, c.zper, ig);
-        load_moments<Codec>(src, g.fstride, c.col + c.plane * (unsigned)zl, p, mn);
-    }
-
+    K::prefetch(c, g, src, pfb, 0);
     float ppA[8], ppB[8], cA[8], cB[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) ppA[k] = ppB[k] = cA[k] = cB[k] = 0.0f;
     // The window rotates by swapping roles between two register sets, so the
     // march advances two planes per loop trip without register copies.
-    bool aborted = false;
     for (int j = 0; j < c.np; j += 2) {
-        aborted = K::plane_step(c, g, p, src, dst, tm, stages, bars, ysm, mn, j, ppA, cA, cB);
-        if (aborted) break;
-        if (j + 1 < c.np) {
-            aborted = K::plane_step(c, g, p, src, dst, tm, stages, bars, ysm, mn, j + 1, ppB, cB, cA);
-            if (aborted) break;
-        }
-    }
-    if constexpr (TMA) {
-        // After a give-up, let every fill already issued land (bounded) before
-        // the CTA exits, so no TMA write targets released shared memory.
-        if (aborted && c.warp == WROWS - 1 && c.lane == 0) {
-            for (int j = c.issued - NSTAGE; j < c.issued; ++j) {
-                if (j < 0) continue;
-                const uint32_t bar = bars + 8u * (j % NSTAGE), par = (uint32_t)((j / NSTAGE) & 1);
-                const long long t0 = clock64();
-                while (!mbar_try_wait(bar, par))
-                    if (clock64() - t0 > 4000000000LL) break;
-            }
-        }
+        K::plane_step(c, g, p, src, dst, ysm, pfb, j, ppA, cA, cB);
+        if (j + 1 < c.np) K::plane_step(c, g, p, src, dst, ysm, pfb, j + 1, ppB, cB, cA);
     }
 }
 
-// ---- host side ------------------------------------------------------------------
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, []() {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(f);
-    });
-    return fn;
-}
-
-template <class Codec>
-bool tma_ok(const tslb_s* h) {
-    const int E = (int)sizeof(typename Codec::T);
-    return ((long long)h->g.nx * E) % 16 == 0 && h->g.nx >= 16 / E && encode_fn() != nullptr;
-}
-
-template <class Codec>
-bool make_maps(const tslb_s* h, const void* src, TmaMaps* tm) {
-    typedef StageLayout<(int)sizeof(typename Codec::T)> SL;
-    const int E = (int)sizeof(typename Codec::T);
-    const Geometry& g = h->g;
-    const CUtensorMapDataType dt = E == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                          : (h->precision == TSLB_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)NFIELDS};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * E, (cuuint64_t)g.plane * E, (cuuint64_t)g.fstride * E};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    const cuuint32_t bmain[4] = {(cuuint32_t)SL::BX, (cuuint32_t)WROWS, 1, 1};
-    const cuuint32_t bcol[4] = {(cuuint32_t)SL::XW, (cuuint32_t)WROWS, 1, 1};
-    const cuuint32_t brow[4] = {(cuuint32_t)SL::BX, 1, 1, 1};
-    const cuuint32_t bcor[4] = {(cuuint32_t)SL::XW, 1, 1, 1};
-    EncodeTiledFn fn = encode_fn();
-    void* gp = const_cast<void*>(src);
-    const cuuint32_t* boxes[4] = {bmain, bcol, brow, bcor};
-    CUtensorMap* outs[4] = {&tm->main, &tm->col, &tm->row, &tm->corner};
-    for (int k = 0; k < 4; ++k) {
-        CUresult r = fn(outs[k], dt, 4, gp, dims, strides, boxes[k], es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return false;
-    }
-    return true;
-}
-
-template <class Codec, bool XFREE, bool TMA>
+template <class Codec, bool XFREE>
 cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    typedef StageLayout<(int)sizeof(typename Codec::T)> SL;
-    auto kern = step_factored_kernel<Codec, XFREE, TMA>;
-    const size_t smem = TMA ? SL::SMEM : 128 + YBYTES;
+    auto kern = step_factored_kernel<Codec, XFREE>;
     static bool configured[64] = {};
     const int dev = h->device;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    constexpr size_t SMEM = smem_bytes<(int)sizeof(typename Codec::T)>();
     if (!configured[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
-    TmaMaps tm;
-    memset(&tm, 0, sizeof(tm));
-    if (TMA && !make_maps<Codec>(h, src, &tm)) return cudaErrorInvalidValue;
     const Geometry& g = h->g;
     const unsigned bx = (unsigned)((g.nx + XOUT - 1) / XOUT);
     const unsigned by = (unsigned)((g.ny + YOUT - 1) / YOUT);
@@ -601,17 +457,15 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
     }
     const int zchunk = (g.nz + best_n - 1) / best_n;
     const unsigned bz = (unsigned)((g.nz + zchunk - 1) / zchunk);
-    kern<<<dim3(bx, by, bz), NT, smem, h->stream>>>((const typename Codec::T*)src, (typename Codec::T*)dst, g, p,
-                                                    zchunk, tm);
+    kern<<<dim3(bx, by, bz), NT, SMEM, h->stream>>>((const typename Codec::T*)src, (typename Codec::T*)dst, g, p,
+                                                   zchunk);
     return cudaGetLastError();
 }
 
 template <class Codec>
 cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    const bool xfree = h->g.bc[0] == TSLB_BC_FREESLIP;
-    const bool tma = tma_ok<Codec>(h) && h->kernel == TSLB_KERNEL_FACTORED_TMA;
-    if (xfree) return tma ? launch_t<Codec, true, true>(h, src, dst, p) : launch_t<Codec, true, false>(h, src, dst, p);
-    return tma ? launch_t<Codec, false, true>(h, src, dst, p) : launch_t<Codec, false, false>(h, src, dst, p);
+    if (h->g.bc[0] == TSLB_BC_FREESLIP) return launch_t<Codec, true>(h, src, dst, p);
+    return launch_t<Codec, false>(h, src, dst, p);
 }
 
 }  // namespace
@@ -619,14 +473,6 @@ cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Phys
 bool factored_supports(const tslb_s* h) {
     // 32-bit node offsets inside a field
     return (long long)h->g.plane * h->g.nz < (1LL << 31);
-}
-
-bool factored_uses_tma(const tslb_s* h) {
-    switch (h->precision) {
-        case TSLB_FP32: return tma_ok<CodecF32>(h) && h->kernel == TSLB_KERNEL_FACTORED_TMA;
-        case TSLB_BF16: return tma_ok<CodecBF16>(h) && h->kernel == TSLB_KERNEL_FACTORED_TMA;
-        default: return tma_ok<CodecF16>(h) && h->kernel == TSLB_KERNEL_FACTORED_TMA;
-    }
 }
 
 cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p) {

@@ -17,8 +17,7 @@ from paper_2401_17074_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = [pytest.param(T.KERNEL_DIRECT, id="direct"), pytest.param(T.KERNEL_FACTORED, id="factored"),
-           pytest.param(T.KERNEL_FACTORED_TMA, id="factored_tma")]
+KERNELS = [pytest.param(T.KERNEL_DIRECT, id="direct"), pytest.param(T.KERNEL_FACTORED, id="factored")]
 FIELDS = ["drho", "ux", "uy", "uz", "pxx", "pyy", "pzz", "pxy", "pxz", "pyz"]
 
 
