@@ -72,7 +72,7 @@ def measured_peaks():
 
 
 def traffic_record(kernel_name, precision):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel source is unchanged since."""
+    """DRAM bytes per launch from a committed ncu capture, if the kernel sources are unchanged since."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -81,11 +81,13 @@ def traffic_record(kernel_name, precision):
     for r in recs:
         if r.get("kernel") != kernel_name or r.get("precision") != precision:
             continue
-        src = os.path.join(ROOT, r["source"])
-        if not os.path.exists(src):
-            return None
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if h != r.get("source_sha256"):
+        h = hashlib.sha256()
+        for src in r["sources"]:
+            path = os.path.join(ROOT, src)
+            if not os.path.exists(path):
+                return None
+            h.update(open(path, "rb").read())
+        if h.hexdigest() != r.get("sources_sha256"):
             return None
         return float(r["bytes_per_launch_full"])
     return None

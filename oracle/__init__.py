@@ -130,7 +130,9 @@ class OracleSim:
     bc = (x-, x+, y-, y+, z-, z+) face codes.  A non-periodic face makes the
     outermost node layer a boundary layer (solid for BOUNCEBACK / FREESLIP,
     ghost for INFLOW / OUTFLOW); only interior nodes are updated.
-    inflow = dict(center2=(cx2, cy2), diameter=D, u_jet=U, noise_amp=a, seed=s).
+    inflow = dict(center2=(cx2, cy2), diameter=D, u_jet=U, noise_amp=a, seed=s[, origin=(ox, oy)]);
+    origin places this box inside a larger lattice for the nozzle mask and the
+    noise counter (a sub-box that reproduces part of a full-size run).
     """
 
     def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, inflow=None):
@@ -139,11 +141,12 @@ class OracleSim:
         d = np.array(self.dims, dtype=np.int64)
         F = _f64(force)
         b = np.array(bc, dtype=np.int32)
-        ii = np.zeros(3, dtype=np.int64)
+        ii = np.zeros(5, dtype=np.int64)
         dd = np.zeros(2)
         seed = 0
         if inflow is not None:
-            ii[:] = [inflow["center2"][0], inflow["center2"][1], inflow["diameter"]]
+            org = inflow.get("origin", (0, 0))
+            ii[:] = [inflow["center2"][0], inflow["center2"][1], inflow["diameter"], org[0], org[1]]
             dd[:] = [inflow["u_jet"], inflow["noise_amp"]]
             seed = int(inflow["seed"])
         st = ctypes.c_int(0)

@@ -198,6 +198,8 @@ struct Inflow {
     double u_jet;        // imposed axial velocity
     double noise_amp;    // relative noise amplitude a: u_z = u_jet (1 + a xi)
     uint64_t seed;
+    int64_t origin[2];   // lattice coordinates of this box's node (0, 0) in a larger lattice
+                         // (lets a sub-box reproduce the nozzle and noise of the full one)
 };
 
 template <class T>
@@ -238,9 +240,10 @@ void source_post(const Sim<T>& s, int64_t x, int64_t y, int64_t z, T out[27]) {
         int64_t nf = s.idx(x, y, 1);
         node_moments(s, nf, rho, u, pi);
         T uB[3] = {0.0, 0.0, 0.0};
-        int64_t dx = 2 * x - s.inflow.center2[0], dy = 2 * y - s.inflow.center2[1];
+        const int64_t X = x + s.inflow.origin[0], Y = y + s.inflow.origin[1];
+        int64_t dx = 2 * X - s.inflow.center2[0], dy = 2 * Y - s.inflow.center2[1];
         if (dx * dx + dy * dy <= s.inflow.diameter * s.inflow.diameter) {
-            double xi = inflow_noise(s.inflow.seed, x, y, s.t);
+            double xi = inflow_noise(s.inflow.seed, X, Y, s.t);
             uB[2] = s.inflow.u_jet * (1.0 + s.inflow.noise_amp * xi);
         }
         T eq[27], neq[27];
@@ -432,7 +435,10 @@ void* orc_create(const int64_t* dims, double tau, const double* F, const int* bc
     Sim<double>* s = new Sim<double>();
     Inflow in;
     std::memset(&in, 0, sizeof(in));
-    if (inflow_i) { in.center2[0] = inflow_i[0]; in.center2[1] = inflow_i[1]; in.diameter = inflow_i[2]; }
+    if (inflow_i) {
+        in.center2[0] = inflow_i[0]; in.center2[1] = inflow_i[1]; in.diameter = inflow_i[2];
+        in.origin[0] = inflow_i[3]; in.origin[1] = inflow_i[4];
+    }
     if (inflow_d) { in.u_jet = inflow_d[0]; in.noise_amp = inflow_d[1]; }
     in.seed = seed;
     int st = validate_and_init(s, dims, tau, F, bc, &in);

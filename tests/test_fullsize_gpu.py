@@ -1,0 +1,162 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+The CUDA step runs on the whole lattice (turbulent channel 512 x 130 x 256,
+round jet 256 x 256 x 640) with the default kernel and FP32 storage.  The
+oracle cannot run those lattices, so it recomputes sampled columns one by one:
+after k steps a node depends only on nodes within distance k, so a small
+oracle box cut out around the column (periodic axes wrapped, wall layers kept,
+one extra fake wall layer beyond the dependency radius where the box is cut
+inside the fluid) reproduces that column exactly.  Samples sit on tile
+boundaries, periodic seams, walls and the nozzle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2401_17074_b300 as T
+from paper_2401_17074_b300 import workloads as W
+
+NSTEPS = 2
+
+
+def _cut(arr, dims, xs, ys, zs):
+    """Full-lattice [..., N] array -> sub-box [..., n] over lattice index lists xs, ys, zs."""
+    nx, ny, nz = dims
+    a = arr.reshape(arr.shape[:-1] + (nz, ny, nx))
+    a = a[..., zs, :, :][..., :, ys, :][..., :, :, xs]
+    return np.ascontiguousarray(a.reshape(arr.shape[:-1] + (-1,)))
+
+
+def _axis_range(c, n, periodic, R):
+    """Lattice indices of a sub-box axis around c, and whether it is periodic."""
+    if periodic:
+        return [(c + d) % n for d in range(-R, R + 1)], True
+    lo, hi = max(0, c - R - 1), min(n - 1, c + R + 1)
+    return list(range(lo, hi + 1)), False
+
+
+def _compare_column(gpu, state_full, dims, tau, force, bc, col, inflow=None):
+    """Run the oracle on the sub-box around column `col` and compare that column.
+
+    col: dict with the two sampled coordinates (the third axis is kept whole).
+    """
+    nx, ny, nz = dims
+    R = NSTEPS
+    axes = []
+    for a, n in enumerate(dims):
+        per = bc[2 * a] == 0
+        if a in col:
+            idx, p = _axis_range(col[a], n, per, R)
+        else:
+            idx, p = list(range(n)), per
+        axes.append((idx, p))
+    xs, ys, zs = axes[0][0], axes[1][0], axes[2][0]
+    sdims = (len(xs), len(ys), len(zs))
+    sbc = []
+    for a in range(3):
+        if axes[a][1]:
+            sbc += [0, 0]
+        else:
+            sbc += [bc[2 * a], bc[2 * a + 1]]
+    rho, u, pi = state_full
+    sub = (_cut(rho, dims, xs, ys, zs), _cut(u, dims, xs, ys, zs), _cut(pi, dims, xs, ys, zs))
+    sin = None
+    if inflow is not None:
+        sin = dict(inflow)
+        sin["origin"] = (xs[0], ys[0])
+    o = oracle.OracleSim(sdims, tau, force=force, bc=tuple(sbc), inflow=sin)
+    o.init_moments(*sub)
+    o.step(NSTEPS)
+    r, uu, pp = o.get_moments()
+    ref = np.concatenate([(r - 1)[None], uu, pp])
+    got = _cut(gpu, dims, xs, ys, zs)
+    # positions of the sampled column inside the sub-box
+    sel = np.zeros((sdims[2], sdims[1], sdims[0]), bool)
+    ix = xs.index(col[0]) if 0 in col else slice(None)
+    iy = ys.index(col[1]) if 1 in col else slice(None)
+    iz = zs.index(col[2]) if 2 in col else slice(None)
+    sel[iz, iy, ix] = True
+    # interior of the full lattice only
+    inner = np.ones((nz, ny, nx), bool)
+    if bc[0]:
+        inner[:, :, [0, nx - 1]] = False
+    if bc[2]:
+        inner[:, [0, ny - 1], :] = False
+    if bc[4]:
+        inner[[0, nz - 1], :, :] = False
+    inner_sub = _cut(inner.reshape(-1).astype(np.float64)[None], dims, xs, ys, zs)[0] > 0.5
+    m = sel.reshape(-1) & inner_sub
+    return got[:, m], ref[:, m]
+
+
+def _run_gpu(prm, state, inflow=None):
+    s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], inflow=inflow)
+    s.init_moments(*state)
+    s.step(NSTEPS)
+    r, u, p = s.get_moments()
+    s.close()
+    return np.concatenate([(r - 1)[None], u, p])
+
+
+def _check(pairs, tol, tol_drho=2e-5):
+    """Relative L2 error per field over the sampled nodes.
+
+    rho - 1 is a small difference of cancelling mass fluxes (the channel starts
+    at rho = 1 exactly), so its FP32 floor relative to its own norm is higher;
+    it gets the same 2e-5 bound as in the Taylor-Green parity test.
+    """
+    got = np.concatenate([g for g, _ in pairs], axis=1)
+    ref = np.concatenate([r for _, r in pairs], axis=1)
+    for k in range(10):
+        nrm = np.linalg.norm(ref[k])
+        err = np.linalg.norm(got[k] - ref[k]) / nrm if nrm > 0 else np.abs(got[k] - ref[k]).max()
+        assert err <= (tol_drho if k == 0 else tol), (k, err)
+
+
+def _oracle_full(prm, state, inflow=None):
+    o = oracle.OracleSim(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], inflow=inflow)
+    o.init_moments(*state)
+    o.step(NSTEPS)
+    r, u, p = o.get_moments()
+    return np.concatenate([(r - 1)[None], u, p])
+
+
+def test_subbox_columns_reproduce_full_oracle():
+    """The column sampler itself: sub-box recomputation equals a full oracle run (CPU)."""
+    prm = W.channel_params(nx=14, ny=12, nz=9)
+    state = W.channel_state(prm, seed=3)
+    full = _oracle_full(prm, state)
+    for col in ({0: 0, 2: 0}, {0: 13, 2: 4}, {0: 6, 2: 8}):
+        got, ref = _compare_column(full, state, prm["dims"], prm["tau"], prm["force"], prm["bc"], col)
+        assert np.abs(got - ref).max() < 1e-15
+    prm = W.jet_params(nx=14, ny=13, nz=10, D=6)
+    state = W.random_state(prm["dims"], seed=4, drho=0.002, du=0.01, dpi=1e-4)
+    full = _oracle_full(prm, state, inflow=prm["inflow"])
+    for col in ({0: 1, 1: 1}, {0: 12, 1: 6}, {0: 7, 1: 6}, {0: 4, 1: 11}):
+        got, ref = _compare_column(full, state, prm["dims"], prm["tau"], prm["force"], prm["bc"], col,
+                                   inflow=prm["inflow"])
+        assert np.abs(got - ref).max() < 1e-15
+
+
+@pytest.mark.gpu
+def test_channel_full_size_sampled(cuda_ok):
+    prm = W.channel_params()  # 512 x 130 x 256
+    state = W.channel_state(prm, seed=1)
+    gpu = _run_gpu(prm, state)
+    cols = [{0: 0, 2: 0}, {0: 511, 2: 255}, {0: 255, 2: 128}, {0: 30, 2: 17}, {0: 29, 2: 200}, {0: 480, 2: 64}]
+    pairs = [_compare_column(gpu, state, prm["dims"], prm["tau"], prm["force"], prm["bc"], c) for c in cols]
+    _check(pairs, 3e-6)
+
+
+@pytest.mark.gpu
+def test_jet_full_size_sampled(cuda_ok):
+    prm = W.jet_params()  # 256 x 256 x 640, inflow z = 0, outflow z = 639, free-slip sides
+    dims = prm["dims"]
+    # small random deviations from rest exercise every term of the step
+    state = W.random_state(dims, seed=41, drho=0.002, du=0.01, dpi=1e-4)
+    gpu = _run_gpu(prm, state, inflow=prm["inflow"])
+    cols = [{0: 1, 1: 1}, {0: 1, 1: 128}, {0: 254, 1: 254}, {0: 127, 1: 128}, {0: 118, 1: 127}, {0: 200, 1: 50},
+            {0: 30, 1: 17}]
+    pairs = [_compare_column(gpu, state, dims, prm["tau"], prm["force"], prm["bc"], c, inflow=prm["inflow"])
+             for c in cols]
+    _check(pairs, 3e-6)
