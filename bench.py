@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -215,9 +216,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, dist, clocks=None):
+def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, dist, clocks=None, keep=False):
+    from paper_2401_17074_b300 import workloads as W
     s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], precision=PREC_CODE[precision],
-                 kernel=kernel, stream=stream.cuda_stream, pi_ref=4e-4)
+                 kernel=kernel, stream=stream.cuda_stream, u_ref=0.05, pi_ref=W.pi_reference(state))
     s.init_moments(*state)
     s.step(warmup)
     torch.cuda.synchronize()
@@ -240,8 +242,47 @@ def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, 
         dist.barrier()
     d, code = s.diagnostics()
     nodes = s.interior_nodes()
+    final = s.get_moments() if keep else None
     s.close()
-    return ms, nodes, d, code, ck
+    return ms, nodes, d, code, ck, final
+
+
+def precision_errors(prm, ref, got):
+    """Relative L2 errors of a 16-bit run against the FP32 run: mean u_x(y) profile and u field."""
+    nx, ny, nz = prm["dims"]
+    prof = lambda u: u[0].reshape(nz, ny, nx)[:, 1:ny - 1, :].mean(axis=(0, 2))
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"mean_ux_profile": rel(prof(got[1]), prof(ref[1])), "u_field": rel(got[1], ref[1]),
+            "pi_field": rel(got[2], ref[2])}
+
+
+def time_adjoint(T, torch, stream, n=128, nsteps=64, k=16, tau=0.52):
+    """Forward (with checkpoints) and discrete adjoint of the force gradient on an n^3 periodic box."""
+    from paper_2401_17074_b300 import workloads as W
+    dims, state = W.divfree_random(n=n, u_rms=0.02, kmax=8, tau=tau, seed=5)
+    s = T.Solver(dims, tau, checkpoint_every=k, stream=stream.cuda_stream)
+    F = torch.zeros(3 * n ** 3, dtype=torch.float32, device="cuda")
+    g = torch.empty(3 * n ** 3, dtype=torch.float32, device="cuda")
+    s.init_moments(*state)
+    s.set_force_field(F)
+    s.step(nsteps)
+    T.tslb_adjoint_force_gradient(s.handle, nsteps, g, T.DEVICE)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.init_moments(*state)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    s.step(nsteps)
+    s.synchronize()
+    t2 = time.perf_counter()
+    T.tslb_adjoint_force_gradient(s.handle, nsteps, g, T.DEVICE)
+    t3 = time.perf_counter()
+    s.close()
+    return {"workload": "%d^3 periodic, %d steps, checkpoint every %d" % (n, nsteps, k),
+            "forward_ms": (t2 - t1) * 1e3, "adjoint_ms": (t3 - t2) * 1e3,
+            "forward_mlups": n ** 3 * nsteps / (t2 - t1) / 1e6,
+            "adjoint_mlups": n ** 3 * nsteps / (t3 - t2) / 1e6,
+            "note": "wall clock; the adjoint recomputes each checkpoint segment"}
 
 
 def time_e2e(T, torch, prm, state, steps, stream):
@@ -295,8 +336,9 @@ def main():
     hbm, hbm_src = measured_peaks()
 
     clocks = ClockSampler(local) if rank == 0 else None
-    ms, nodes, diag, code, ck = time_device(T, torch, prm, state, args.precision, kernel, args.steps, args.warmup,
-                                            stream, dist, clocks)
+    ms, nodes, diag, code, ck, ref_final = time_device(T, torch, prm, state, args.precision, kernel, args.steps,
+                                                       args.warmup, stream, dist, clocks,
+                                                       keep=not args.no_variants and rank == 0)
     total_nodes = nodes * ws
     value = total_nodes * args.steps / (ms * 1e-3) / 1e6
     launch_s = ms * 1e-3 / args.steps
@@ -311,16 +353,23 @@ def main():
         for prec in ("bf16", "fp16"):
             if prec == args.precision:
                 continue
-            msv, nv, dv, cv, _ = time_device(T, torch, prm, state, prec, kernel, args.steps, args.warmup, stream, dist)
+            msv, nv, dv, cv, _, fin = time_device(T, torch, prm, state, prec, kernel, args.steps, args.warmup,
+                                                  stream, dist, keep=ref_final is not None)
             ls = msv * 1e-3 / args.steps
             variants[prec] = {"value": nv * ws * args.steps / (msv * 1e-3) / 1e6, "unit": "MLUPS",
                               "roofline_frac": BYTES_PER_NODE[prec] * nv / ls / 1e9 / hbm,
                               "bytes_per_node": BYTES_PER_NODE[prec], "stable": cv == T.TSLB_OK}
+            if fin is not None:
+                variants[prec]["error_vs_fp32_after_%d_steps" % (args.steps + args.warmup)] = \
+                    precision_errors(prm, ref_final, fin)
         if args.precision != "fp32":
             pass
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = time_e2e(T, torch, prm, state, args.steps, stream)
+    adj = None
+    if not args.no_adjoint and rank == 0:
+        adj = time_adjoint(T, torch, stream)
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(prm, args.cpu_seconds)
@@ -342,6 +391,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
+            "adjoint": adj,
             "clocks": ck,
             "diagnostics_after_timed": {"mass": diag["mass"], "max_speed": diag["max_speed"], "status": code},
         }

@@ -45,6 +45,11 @@ def random_state(dims, seed, drho=0.01, du=0.05, dpi=1e-3):
     return _pack(rho, list(u), list(pi))
 
 
+def pi_reference(state, headroom=2.0, floor=1e-6):
+    """Scale of Pi^neq for 16-bit storage: headroom x the largest |Pi^neq| of a state."""
+    return max(floor, headroom * float(np.abs(state[2]).max()))
+
+
 def rest_state(dims):
     N = dims[0] * dims[1] * dims[2]
     return _pack(np.ones(N), [np.zeros(N)] * 3, [np.zeros(N)] * 6)

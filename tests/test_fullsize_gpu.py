@@ -99,18 +99,21 @@ def _run_gpu(prm, state, inflow=None):
 
 
 def _check(pairs, tol, tol_drho=2e-5):
-    """Relative L2 error per field over the sampled nodes.
+    """Relative L2 errors over the sampled nodes, per field group.
 
-    rho - 1 is a small difference of cancelling mass fluxes (the channel starts
-    at rho = 1 exactly), so its FP32 floor relative to its own norm is higher;
-    it gets the same 2e-5 bound as in the Taylor-Green parity test.
+    u and Pi^neq are compared as tensors (error norm over all components
+    against the norm of the whole tensor): single components can start at
+    exactly zero (the channel's Pi_xx, Pi_yy, Pi_zz) and are then meaningless
+    as relative errors.  rho - 1 is a small difference of cancelling mass
+    fluxes (the channel starts at rho = 1 exactly), so its FP32 floor relative
+    to its own norm is higher; it gets the same 2e-5 bound as in the
+    Taylor-Green parity test.
     """
     got = np.concatenate([g for g, _ in pairs], axis=1)
     ref = np.concatenate([r for _, r in pairs], axis=1)
-    for k in range(10):
-        nrm = np.linalg.norm(ref[k])
-        err = np.linalg.norm(got[k] - ref[k]) / nrm if nrm > 0 else np.abs(got[k] - ref[k]).max()
-        assert err <= (tol_drho if k == 0 else tol), (k, err)
+    for name, rows, bound in (("drho", [0], tol_drho), ("u", [1, 2, 3], tol), ("pi", [4, 5, 6, 7, 8, 9], tol)):
+        err = np.linalg.norm(got[rows] - ref[rows]) / np.linalg.norm(ref[rows])
+        assert err <= bound, (name, err)
 
 
 def _oracle_full(prm, state, inflow=None):
