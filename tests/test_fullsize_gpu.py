@@ -98,7 +98,7 @@ def _run_gpu(prm, state, inflow=None):
     return np.concatenate([(r - 1)[None], u, p])
 
 
-def _check(pairs, tol, tol_drho=2e-5):
+def _check(pairs, tol, tol_drho=2e-5, tol_pi=None):
     """Relative L2 errors over the sampled nodes, per field group.
 
     u and Pi^neq are compared as tensors (error norm over all components
@@ -111,7 +111,8 @@ def _check(pairs, tol, tol_drho=2e-5):
     """
     got = np.concatenate([g for g, _ in pairs], axis=1)
     ref = np.concatenate([r for _, r in pairs], axis=1)
-    for name, rows, bound in (("drho", [0], tol_drho), ("u", [1, 2, 3], tol), ("pi", [4, 5, 6, 7, 8, 9], tol)):
+    tol_pi = tol if tol_pi is None else tol_pi
+    for name, rows, bound in (("drho", [0], tol_drho), ("u", [1, 2, 3], tol), ("pi", [4, 5, 6, 7, 8, 9], tol_pi)):
         err = np.linalg.norm(got[rows] - ref[rows]) / np.linalg.norm(ref[rows])
         assert err <= bound, (name, err)
 
@@ -148,7 +149,10 @@ def test_channel_full_size_sampled(cuda_ok):
     gpu = _run_gpu(prm, state)
     cols = [{0: 0, 2: 0}, {0: 511, 2: 255}, {0: 255, 2: 128}, {0: 30, 2: 17}, {0: 29, 2: 200}, {0: 480, 2: 64}]
     pairs = [_compare_column(gpu, state, prm["dims"], prm["tau"], prm["force"], prm["bc"], c) for c in cols]
-    _check(pairs, 3e-6)
+    # Pi^neq = sum f c c - rho u u - ... is here ~36x smaller than the rho u u
+    # terms it is computed from (u_x ~ 0.06, Pi ~ 1e-4), so its FP32 floor after
+    # two steps is ~1e-5 relative; u keeps the 3e-6 bound.
+    _check(pairs, 3e-6, tol_pi=2e-5)
 
 
 @pytest.mark.gpu
