@@ -18,7 +18,8 @@
 // marches z, so z-neighbours are the previous / next loop iterations), then y
 // through shared memory (warps are rows), then x through warp shuffles
 // (lanes are columns).  Halo: lanes 0 and 31 and the first and last warp
-// recompute the border columns / rows of the tile.  The z pass starts from
+// recompute the border columns / rows of the tile; the halo warps stop after
+// feeding the y exchange.  The z pass starts from
 // the unscaled Hermite coefficients with the mode scale factors folded into
 // its fused multiply-adds.
 //
@@ -32,7 +33,9 @@
 // population entering from the wall side is the node's own population leaving
 // towards it: specular reflection); a bounce-back y face zeroes the entering
 // deviation and adds the reversed populations of the node itself (halfway
-// bounce-back); inflow / outflow z faces enter the march as ghost planes
+// bounce-back), whose moments the warp of the ghost row beyond the wall
+// computes in closed form one march step ahead, so that the wall rows carry
+// no extra work; inflow / outflow z faces enter the march as ghost planes
 // (Eq. neq_final for the inflow, the adjacent layer's moments for the
 // outflow, Sec. 3.2).
 #include <algorithm>
@@ -62,8 +65,11 @@ struct Prefetch {
     static constexpr int B2 = 2 * E;   // bytes per thread of V2
     static constexpr size_t BUF = (size_t)(2 * B01 + B2) * NT;
 };
+// Bounce-back corrections: [2 buffers][2 walls][NCORR sums][32 lanes].
+constexpr int NCORR = 10;
+constexpr size_t CORRBUF = sizeof(float) * 2 * 2 * NCORR * 32;
 template <int E>
-constexpr size_t smem_bytes() { return 2 * YBUF + 2 * Prefetch<E>::BUF; }
+constexpr size_t smem_bytes() { return 2 * YBUF + 2 * Prefetch<E>::BUF + CORRBUF; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 template <int BYTES>
@@ -169,12 +175,25 @@ __device__ __forceinline__ void zpops(const Herm& h, Pops P[8]) {
     }
 }
 
+// Body force at stored node idx: the uniform force, or the force field.
+__device__ __forceinline__ void load_force(const Physics& p, const Geometry& g, unsigned idx, float& F0, float& F1,
+                                           float& F2) {
+    F0 = p.F[0];
+    F1 = p.F[1];
+    F2 = p.F[2];
+    if (p.force) {
+        F0 = __ldg(p.force + idx);
+        F1 = __ldg(p.force + g.fstride + idx);
+        F2 = __ldg(p.force + 2 * g.fstride + idx);
+    }
+}
+
 // Per-thread constants of the march.
 struct Ctx {
     int tid, lane, warp, x, y, xl, yl;
     unsigned col, plane;
     int z0, z1, np;  // march covers planes z0-1 .. z1 (np of them)
-    bool zper, ybb, store, row_lo, row_hi, zero_row, xlo_mirror, xhi_mirror;
+    bool zper, ybb, store, out_row, row_lo, row_hi, zero_row, xlo_mirror, xhi_mirror;
     int offLv, offRv, offLs, offRs;  // y-exchange read offsets (float4 / float units, relative to a slot base)
 };
 
@@ -202,8 +221,8 @@ struct Kernel {
 
     static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
                                                       const T* __restrict__ src, T* __restrict__ dst, float* ysm,
-                                                      char* pfb, int j, float (&ppOld)[8], const float (&cOld)[8],
-                                                      float (&cNew)[8]) {
+                                                      char* pfb, float* corr, int j, float (&ppOld)[8],
+                                                      const float (&cOld)[8], float (&cNew)[8]) {
         const int zs = c.z0 - 1 + j;
         bool inflow_ghost;
         const int zl = plane_of(zs, g, c.zper, inflow_ghost);
@@ -212,33 +231,36 @@ struct Kernel {
         if (zs < c.z1) prefetch(c, g, src, pfb, j + 1);
         else cp_async_commit();
         cp_async_wait_prev();
-        float m[NFIELDS];
-        {
-            const char* b = pfb + (j & 1) * PF::BUF;
-            const T* v0 = reinterpret_cast<const T*>(b + c.tid * PF::B01);
-            const T* v1 = reinterpret_cast<const T*>(b + NT * PF::B01 + c.tid * PF::B01);
-            const T* v2 = reinterpret_cast<const T*>(b + 2 * NT * PF::B01 + c.tid * PF::B2);
-            NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
-        }
+        const char* pb = pfb + (j & 1) * PF::BUF;
+        const T* v0 = reinterpret_cast<const T*>(pb + c.tid * PF::B01);
+        const T* v1 = reinterpret_cast<const T*>(pb + NT * PF::B01 + c.tid * PF::B01);
+        const T* v2 = reinterpret_cast<const T*>(pb + 2 * NT * PF::B01 + c.tid * PF::B2);
         // ---- source plane: moments -> Hermite coefficients -> z populations ----
-        Herm h;
-        if (inflow_ghost) {
-            const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
-            h = hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f, p.omega1);
-        } else {
-            float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
-            if (p.force) {
-                F0 = __ldg(p.force + idx);
-                F1 = __ldg(p.force + g.fstride + idx);
-                F2 = __ldg(p.force + 2 * g.fstride + idx);
-            }
-            h = hermite(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
-                        p.omega1);
-        }
         Pops P[8];
-        zpops(h, P);
+        if (!c.zero_row) {
+            float m[NFIELDS];
+            NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
+            Herm h;
+            if (inflow_ghost) {
+                const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
+                h = hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
+                            p.omega1);
+            } else {
+                float F0, F1, F2;
+                load_force(p, g, idx, F0, F1, F2);
+                h = hermite(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
+                            p.omega1);
+            }
+            zpops(h, P);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) P[k] = {0.0f, 0.0f, 0.0f};
+        }
 
         if (zs >= c.z0 + 1) {
+            float* sb = ysm + (j & 1) * (YBUF / sizeof(float));
+            float4* sv = reinterpret_cast<float4*>(sb);
+            float* ss = sb + 4 * YV * NT;
             // ---- z moments of plane z = zs - 1 ------------------------------
             float Z[8][3];
 #pragma unroll
@@ -256,9 +278,6 @@ struct Kernel {
                 Q[3 + r] = pops3(Z[1][r], Z[5][r], Z[7][r]);  // k1 = 1
                 Q[6 + r] = pops2(Z[3][r], Z[6][r]);           // k1 = 2
             }
-            float* sb = ysm + (j & 1) * (YBUF / sizeof(float));
-            float4* sv = reinterpret_cast<float4*>(sb);
-            float* ss = sb + 4 * YV * NT;
             if (c.zero_row) {
                 // ghost row beyond a bounce-back wall: the entering deviation is zero
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -275,92 +294,79 @@ struct Kernel {
                 ss[NT + c.tid] = Q[8].pm;
             }
             __syncthreads();
-            float L[9], R[9];
-            {
-                const float4 l0 = sv[0 * NT + c.offLv], l1 = sv[1 * NT + c.offLv];
-                const float4 r0 = sv[2 * NT + c.offRv], r1 = sv[3 * NT + c.offRv];
-                L[0] = l0.x; L[1] = l0.y; L[2] = l0.z; L[3] = l0.w;
-                L[4] = l1.x; L[5] = l1.y; L[6] = l1.z; L[7] = l1.w;
-                R[0] = r0.x; R[1] = r0.y; R[2] = r0.z; R[3] = r0.w;
-                R[4] = r1.x; R[5] = r1.y; R[6] = r1.z; R[7] = r1.w;
-                L[8] = ss[c.offLs];
-                R[8] = ss[NT + c.offRs];
-            }
-            // Y[k1][q][r] for (q, r) in {(0,0),(1,0),(2,0),(0,1),(1,1),(0,2)}
-            float Y[3][6];
+            // halo and ghost rows only feed the y exchange (warp-uniform)
+            if (c.out_row) {
+                float L[9], R[9];
+                {
+                    const float4 l0 = sv[0 * NT + c.offLv], l1 = sv[1 * NT + c.offLv];
+                    const float4 r0 = sv[2 * NT + c.offRv], r1 = sv[3 * NT + c.offRv];
+                    L[0] = l0.x; L[1] = l0.y; L[2] = l0.z; L[3] = l0.w;
+                    L[4] = l1.x; L[5] = l1.y; L[6] = l1.z; L[7] = l1.w;
+                    R[0] = r0.x; R[1] = r0.y; R[2] = r0.z; R[3] = r0.w;
+                    R[4] = r1.x; R[5] = r1.y; R[6] = r1.z; R[7] = r1.w;
+                    L[8] = ss[c.offLs];
+                    R[8] = ss[NT + c.offRs];
+                }
+                // Y[k1][q][r] for (q, r) in {(0,0),(1,0),(2,0),(0,1),(1,1),(0,2)}
+                float Y[3][6];
 #pragma unroll
-            for (int k1 = 0; k1 < 3; ++k1) {
+                for (int k1 = 0; k1 < 3; ++k1) {
 #pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    const int jj = 3 * k1 + r;
-                    const float sLR = L[jj] + R[jj];
-                    if (r == 0) {
-                        Y[k1][0] = fmaf(4.0f, Q[jj].c, sLR);  // q = 0
-                        Y[k1][1] = L[jj] - R[jj];              // q = 1
-                        Y[k1][2] = sLR;                        // q = 2
-                    } else if (r == 1) {
-                        Y[k1][3] = fmaf(4.0f, Q[jj].c, sLR);  // (q, r) = (0, 1)
-                        Y[k1][4] = L[jj] - R[jj];              // (1, 1)
-                    } else {
-                        Y[k1][5] = fmaf(4.0f, Q[jj].c, sLR);  // (0, 2)
+                    for (int r = 0; r < 3; ++r) {
+                        const int jj = 3 * k1 + r;
+                        const float sLR = L[jj] + R[jj];
+                        if (r == 0) {
+                            Y[k1][0] = fmaf(4.0f, Q[jj].c, sLR);  // q = 0
+                            Y[k1][1] = L[jj] - R[jj];              // q = 1
+                            Y[k1][2] = sLR;                        // q = 2
+                        } else if (r == 1) {
+                            Y[k1][3] = fmaf(4.0f, Q[jj].c, sLR);  // (q, r) = (0, 1)
+                            Y[k1][4] = L[jj] - R[jj];              // (1, 1)
+                        } else {
+                            Y[k1][5] = fmaf(4.0f, Q[jj].c, sLR);  // (0, 2)
+                        }
                     }
                 }
-            }
-            // ---- x pass: groups (q, r) over k1 ------------------------------
-            float Mo[6][3];
+                // ---- x pass: groups (q, r) over k1 --------------------------
+                float Mo[6][3];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const Pops X = pops3(Y[0][k], Y[1][k], Y[2][k]);
-                float Lx = __shfl_up_sync(0xffffffffu, X.pp, 1);
-                float Rx = __shfl_down_sync(0xffffffffu, X.pm, 1);
-                if (XFREE) {
-                    if (c.xlo_mirror) Lx = X.pm;
-                    if (c.xhi_mirror) Rx = X.pp;
-                }
-                const float sLR = Lx + Rx;
-                Mo[k][0] = fmaf(4.0f, X.c, sLR);
-                Mo[k][1] = Lx - Rx;
-                Mo[k][2] = sLR;
-            }
-            float D0 = Mo[0][0];
-            float J[3] = {Mo[0][1], Mo[1][0], Mo[3][0]};
-            float S[6] = {Mo[0][2], Mo[2][0], Mo[5][0], Mo[1][1], Mo[3][1], Mo[4][0]};
-            const int z = zs - 1;
-            const unsigned oidx = c.col + c.plane * (unsigned)z;
-            // ---- halfway bounce-back on the wall-adjacent rows --------------
-            if (c.ybb && (c.row_lo || c.row_hi)) {
-                float mo[NFIELDS];
-                NodeIO<Codec>::load(src, g.fstride, oidx, p, mo);
-                float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
-                if (p.force) {
-                    F0 = __ldg(p.force + oidx);
-                    F1 = __ldg(p.force + g.fstride + oidx);
-                    F2 = __ldg(p.force + 2 * g.fstride + oidx);
-                }
-                float Ao[NMODES];
-                post_modes(mo[F_DRHO], mo[F_UX], mo[F_UY], mo[F_UZ], mo[F_UX], mo[F_UY], mo[F_UZ], &mo[F_PXX], F0,
-                           F1, F2, p.omega1, Ao);
-                const int cy = c.row_lo ? 1 : -1;  // direction arriving from the wall
-#pragma unroll
-                for (int cz = -1; cz <= 1; ++cz)
-#pragma unroll
-                    for (int cx = -1; cx <= 1; ++cx) {
-                        const float gi = pop_dev216(Ao, -cx, -cy, -cz);
-                        D0 += gi;
-                        J[0] = fmaf(gi, (float)cx, J[0]);
-                        J[1] = fmaf(gi, (float)cy, J[1]);
-                        J[2] = fmaf(gi, (float)cz, J[2]);
-                        S[0] = fmaf(gi, (float)(cx * cx), S[0]);
-                        S[1] += gi;
-                        S[2] = fmaf(gi, (float)(cz * cz), S[2]);
-                        S[3] = fmaf(gi, (float)(cx * cy), S[3]);
-                        S[4] = fmaf(gi, (float)(cx * cz), S[4]);
-                        S[5] = fmaf(gi, (float)(cy * cz), S[5]);
+                for (int k = 0; k < 6; ++k) {
+                    const Pops X = pops3(Y[0][k], Y[1][k], Y[2][k]);
+                    float Lx = __shfl_up_sync(0xffffffffu, X.pp, 1);
+                    float Rx = __shfl_down_sync(0xffffffffu, X.pm, 1);
+                    if (XFREE) {
+                        if (c.xlo_mirror) Lx = X.pm;
+                        if (c.xhi_mirror) Rx = X.pp;
                     }
+                    const float sLR = Lx + Rx;
+                    Mo[k][0] = fmaf(4.0f, X.c, sLR);
+                    Mo[k][1] = Lx - Rx;
+                    Mo[k][2] = sLR;
+                }
+                float D0 = Mo[0][0];
+                float J[3] = {Mo[0][1], Mo[1][0], Mo[3][0]};
+                float S[6] = {Mo[0][2], Mo[2][0], Mo[5][0], Mo[1][1], Mo[3][1], Mo[4][0]};
+                // ---- halfway bounce-back on the wall-adjacent rows ----------
+                // The ghost row next to the wall computed the correction for
+                // this plane one march step earlier (see bounce_back_correction).
+                if (c.ybb) {
+#pragma unroll
+                    for (int side = 0; side < 2; ++side) {
+                        if (side == 0 ? !c.row_lo : !c.row_hi) continue;
+                        const float* cb = corr + (((j + 1) & 1) * 2 + side) * NCORR * 32 + c.lane;
+                        D0 += cb[0 * 32];
+                        J[0] += cb[1 * 32];
+                        J[1] += cb[2 * 32];
+                        J[2] += cb[3 * 32];
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) S[k] += cb[(4 + k) * 32];
+                    }
+                }
+                float out[NFIELDS];
+                finish_moments(D0, J, S, out);
+                const unsigned oidx = c.col + c.plane * (unsigned)(zs - 1);
+                if (c.store) NodeIO<Codec>::store(dst, g.fstride, oidx, p, out);
             }
-            float out[NFIELDS];
-            finish_moments(D0, J, S, out);
-            if (c.store) NodeIO<Codec>::store(dst, g.fstride, oidx, p, out);
         }
         // ---- advance the z window --------------------------------------------
 #pragma unroll
@@ -368,6 +374,47 @@ struct Kernel {
             ppOld[k] = P[k].pp;
             cNew[k] = P[k].c;
         }
+        if (c.zero_row && zs >= c.z0 && zs < c.z1) {
+            // The ghost thread's column is clamped onto the wall-adjacent node,
+            // so its prefetch slots hold that node's moments at plane zs.
+            float m[NFIELDS];
+            NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
+            float F0, F1, F2;
+            load_force(p, g, idx, F0, F1, F2);
+            bounce_back_correction(m, F0, F1, F2, p.omega1, c.y < 0 ? 1.0f : -1.0f,
+                                   corr + ((j & 1) * 2 + (c.y < 0 ? 0 : 1)) * NCORR * 32 + c.lane);
+        }
+    }
+
+    // Halfway bounce-back at a y wall: the nine populations entering the
+    // wall-adjacent node from the wall are its own populations leaving towards
+    // the wall, reversed.  By orthogonality of the 1-D basis their moments
+    // need only the y-contractions B_kx,kz = A_kx0kz + phi_1(-s) A_kx1kz +
+    // 2 A_kx2kz of the post-collision modes at the leaving direction -s, and
+    // the 1-D sums 6 (order 0), 2 (c phi_1) and 2 A_0 + 4 A_2 (c^2).
+    // s = +1 for the wall below the node, -1 for the wall above.  Writes the
+    // 216-scaled additions to D0, J, S (stride 32 floats).
+    static __device__ __forceinline__ void bounce_back_correction(const float m[NFIELDS], float F0, float F1, float F2,
+                                                                  float omega1, float s, float* out) {
+        float Ao[NMODES];
+        post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, omega1, Ao);
+        const float B00 = fmaf(2.0f, Ao[M020], fmaf(-s, Ao[M010], Ao[M000]));
+        const float B10 = fmaf(2.0f, Ao[M120], fmaf(-s, Ao[M110], Ao[M100]));
+        const float B01 = fmaf(2.0f, Ao[M021], fmaf(-s, Ao[M011], Ao[M001]));
+        const float B20 = fmaf(-s, Ao[M210], Ao[M200]);
+        const float B02 = fmaf(-s, Ao[M012], Ao[M002]);
+        const float B11 = fmaf(-s, Ao[M111], Ao[M101]);
+        const float b36 = 36.0f * B00, b12 = 12.0f * B00, s12 = -12.0f * s;
+        out[0 * 32] = b36;                      // D0
+        out[1 * 32] = -12.0f * B10;             // J_x
+        out[2 * 32] = s * b36;                  // J_y
+        out[3 * 32] = -12.0f * B01;             // J_z
+        out[4 * 32] = fmaf(24.0f, B20, b12);    // S_xx
+        out[5 * 32] = b36;                      // S_yy
+        out[6 * 32] = fmaf(24.0f, B02, b12);    // S_zz
+        out[7 * 32] = s12 * B10;                // S_xy
+        out[8 * 32] = 4.0f * B11;               // S_xz
+        out[9 * 32] = s12 * B01;                // S_yz
     }
 };
 
@@ -378,6 +425,7 @@ __global__ void __launch_bounds__(NT, 1)
     typedef Kernel<Codec, XFREE> K;
     extern __shared__ __align__(16) float ysm[];  // [2][YBUF] y exchange, then [2][PF::BUF] plane prefetch
     char* pfb = reinterpret_cast<char*>(ysm) + 2 * YBUF;
+    float* corr = reinterpret_cast<float*>(pfb + 2 * K::PF::BUF);
 
     Ctx c;
     c.tid = threadIdx.x;
@@ -394,6 +442,7 @@ __global__ void __launch_bounds__(NT, 1)
     c.yl = yper ? (c.y + g.ny) % g.ny : min(max(c.y, 0), g.ny - 1);
     c.col = (unsigned)c.xl + (unsigned)g.nx * (unsigned)c.yl;
     c.plane = (unsigned)g.plane;
+    c.out_row = c.warp >= 1 && c.warp <= YOUT && (yper || (c.y >= 0 && c.y < g.ny));
     c.store = c.lane >= 1 && c.lane <= XOUT && c.x < g.nx && c.warp >= 1 && c.warp <= YOUT && c.y < g.ny;
     c.xlo_mirror = XFREE && c.x == 0;
     c.xhi_mirror = XFREE && c.x == g.nx - 1;
@@ -419,8 +468,8 @@ __global__ void __launch_bounds__(NT, 1)
     // The window rotates by swapping roles between two register sets, so the
     // march advances two planes per loop trip without register copies.
     for (int j = 0; j < c.np; j += 2) {
-        K::plane_step(c, g, p, src, dst, ysm, pfb, j, ppA, cA, cB);
-        if (j + 1 < c.np) K::plane_step(c, g, p, src, dst, ysm, pfb, j + 1, ppB, cB, cA);
+        K::plane_step(c, g, p, src, dst, ysm, pfb, corr, j, ppA, cA, cB);
+        if (j + 1 < c.np) K::plane_step(c, g, p, src, dst, ysm, pfb, corr, j + 1, ppB, cB, cA);
     }
 }
 

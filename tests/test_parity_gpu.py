@@ -128,6 +128,17 @@ def test_bounceback_random_state(cuda_ok, kernel):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("dims", [(6, 4, 5), (33, 18, 6), (40, 38, 7)], ids=["two-rows", "one-tile", "ragged-tiles"])
+def test_bounceback_wall_rows(cuda_ok, kernel, dims):
+    """Two interior rows (each next to a wall); interior height equal to one y
+    tile; a ragged last tile whose ghost row above the wall sits inside it."""
+    bc = (0, 0, 1, 1, 0, 0)
+    state = W.random_state(dims, seed=27)
+    errs, _, _ = run_pair(dims, 0.6, state, 3, kernel, bc=bc, force=(2e-5, -1e-5, 1e-5))
+    assert_all_below(errs, 3e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_freeslip_random_state(cuda_ok, kernel):
     dims = (7, 6, 5)
     bc = (2, 2, 2, 2, 0, 0)
