@@ -188,6 +188,11 @@ __device__ __forceinline__ void load_force(const Physics& p, const Geometry& g, 
     }
 }
 
+// Warp-uniform copy of a flag that is equal on all lanes of the warp.  The
+// vote lets the compiler see the branch as non-divergent, so the march's
+// warp-uniform bookkeeping stays on the uniform datapath.
+__device__ __forceinline__ bool uni(bool v) { return __all_sync(0xffffffffu, v); }
+
 // Per-thread constants of the march.
 struct Ctx {
     int tid, lane, warp, x, y, xl, yl;
@@ -237,7 +242,7 @@ struct Kernel {
         const T* v2 = reinterpret_cast<const T*>(pb + 2 * NT * PF::B01 + c.tid * PF::B2);
         // ---- source plane: moments -> Hermite coefficients -> z populations ----
         Pops P[8];
-        if (!c.zero_row) {
+        {
             float m[NFIELDS];
             NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
             Herm h;
@@ -252,9 +257,6 @@ struct Kernel {
                             p.omega1);
             }
             zpops(h, P);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) P[k] = {0.0f, 0.0f, 0.0f};
         }
 
         if (zs >= c.z0 + 1) {
@@ -278,7 +280,7 @@ struct Kernel {
                 Q[3 + r] = pops3(Z[1][r], Z[5][r], Z[7][r]);  // k1 = 1
                 Q[6 + r] = pops2(Z[3][r], Z[6][r]);           // k1 = 2
             }
-            if (c.zero_row) {
+            if (uni(c.zero_row)) {
                 // ghost row beyond a bounce-back wall: the entering deviation is zero
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -295,7 +297,7 @@ struct Kernel {
             }
             __syncthreads();
             // halo and ghost rows only feed the y exchange (warp-uniform)
-            if (c.out_row) {
+            if (uni(c.out_row)) {
                 float L[9], R[9];
                 {
                     const float4 l0 = sv[0 * NT + c.offLv], l1 = sv[1 * NT + c.offLv];
@@ -352,7 +354,7 @@ struct Kernel {
                 if (c.ybb) {
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
-                        if (side == 0 ? !c.row_lo : !c.row_hi) continue;
+                        if (!uni(side == 0 ? c.row_lo : c.row_hi)) continue;
                         const float* cb = corr + (((j + 1) & 1) * 2 + side) * NCORR * 32 + c.lane;
                         D0 += cb[0 * 32];
                         J[0] += cb[1 * 32];
@@ -374,7 +376,7 @@ struct Kernel {
             ppOld[k] = P[k].pp;
             cNew[k] = P[k].c;
         }
-        if (c.zero_row && zs >= c.z0 && zs < c.z1) {
+        if (uni(c.zero_row) && zs >= c.z0 && zs < c.z1) {
             // The ghost thread's column is clamped onto the wall-adjacent node,
             // so its prefetch slots hold that node's moments at plane zs.
             float m[NFIELDS];
