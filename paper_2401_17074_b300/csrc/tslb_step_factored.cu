@@ -19,9 +19,12 @@
 // through shared memory (warps are rows), then x through warp shuffles
 // (lanes are columns).  Halo: lanes 0 and 31 and the first and last warp
 // recompute the border columns / rows of the tile; the halo warps stop after
-// feeding the y exchange.  The z pass starts from
-// the unscaled Hermite coefficients with the mode scale factors folded into
-// its fused multiply-adds.
+// feeding the y exchange.  The z pass starts from the unscaled Hermite
+// coefficients with the mode scale factors folded into its fused
+// multiply-adds.  The regular stages run on packed FP32x2 instructions over
+// pairs of independent groups of the same node (z moments: group pairs; y
+// moments: the r = 0, 1 pair of each k1; x pass: output group pairs), which
+// halves their issue slots while every value is rounded as in scalar code.
 //
 // Memory path: each thread copies its column's moments one plane ahead into
 // its own shared-memory slots (three cp.async vector copies, L1-cached so the
@@ -34,8 +37,8 @@
 // towards it: specular reflection); a bounce-back y face zeroes the entering
 // deviation and adds the reversed populations of the node itself (halfway
 // bounce-back), whose moments the warp of the ghost row beyond the wall
-// computes in closed form one march step ahead, so that the wall rows carry
-// no extra work; inflow / outflow z faces enter the march as ghost planes
+// computes in closed form one march step ahead (six y-contracted mode sums),
+// so that the wall rows only add them in; inflow / outflow z faces enter the march as ghost planes
 // (Eq. neq_final for the inflow, the adjacent layer's moments for the
 // outflow, Sec. 3.2).
 #include <algorithm>
@@ -65,8 +68,9 @@ struct Prefetch {
     static constexpr int B2 = 2 * E;   // bytes per thread of V2
     static constexpr size_t BUF = (size_t)(2 * B01 + B2) * NT;
 };
-// Bounce-back corrections: [2 buffers][2 walls][NCORR sums][32 lanes].
-constexpr int NCORR = 10;
+// Bounce-back corrections: [2 buffers][2 walls][32 lanes][NCORR] (six
+// y-contracted mode sums per lane, padded to eight floats).
+constexpr int NCORR = 8;
 constexpr size_t CORRBUF = sizeof(float) * 2 * 2 * NCORR * 32;
 template <int E>
 constexpr size_t smem_bytes() { return 2 * YBUF + 2 * Prefetch<E>::BUF + CORRBUF; }
@@ -88,6 +92,23 @@ __device__ __forceinline__ Pops pops3(float a0, float a1, float a2) {
     return {e + a1, e - a1, a0 - a2};
 }
 __device__ __forceinline__ Pops pops2(float a0, float a1) { return {a0 + a1, a0 - a1, a0}; }
+
+// Packed FP32x2 arithmetic: two independent mode groups of one node per
+// instruction (each lane rounds exactly like the scalar operation).
+typedef float2 f2;
+__device__ __forceinline__ f2 k2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, k2(-1.0f), a); }  // a - b, one rounding
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+// 1-D populations of two groups: p+, p- and c = a0 - a2.
+struct Pops2 {
+    f2 pp, pm, c;
+};
+__device__ __forceinline__ Pops2 pops3(f2 a0, f2 a1, f2 a2) {
+    const f2 e = fma2(k2(2.0f), a2, a0);
+    return {add2(e, a1), sub2(e, a1), sub2(a0, a2)};
+}
 
 // Interior plane stored at march position zs (periodic wrap, inflow / outflow ghosts).
 __device__ __forceinline__ int plane_of(int zs, const Geometry& g, bool zper, bool& inflow_ghost) {
@@ -140,38 +161,27 @@ __device__ __forceinline__ Herm hermite(float drho, float ux, float uy, float uz
 //   (010, 011, 012) = (3 j_y, 9 h_yz, 4.5 h_yzz), (200, 201) = (1.5 h_xx, 4.5 h_xxz),
 //   (020, 021) = (1.5 h_yy, 4.5 h_yyz), (110, 111) = (9 h_xy, 27 h_xyz), 210 = 4.5 h_xxy,
 //   120 = 4.5 h_xyy, with the scale factors folded into the multiply-adds.
-__device__ __forceinline__ void zpops(const Herm& h, Pops P[8]) {
+// Pairs of groups in the z pass: G0 = (0, 5), G1 = (1, 2), G2 = (3, 4), G3 = (6, 7).
+__device__ __forceinline__ void zpops(const Herm& h, Pops2 P[4]) {
     {
-        const float e = fmaf(3.0f, h.zz, h.drho);
-        P[0] = {fmaf(3.0f, h.jz, e), fmaf(-3.0f, h.jz, e), fmaf(-1.5f, h.zz, h.drho)};
+        const f2 e = make_float2(fmaf(3.0f, h.zz, h.drho), 9.0f * h.xy);
+        const f2 q = make_float2(h.jz, h.xyz);
+        P[0] = {fma2(make_float2(3.0f, 27.0f), q, e), fma2(make_float2(-3.0f, -27.0f), q, e),
+                make_float2(fmaf(-1.5f, h.zz, h.drho), e.y)};
     }
     {
-        const float t = 3.0f * h.jx, e = fmaf(9.0f, h.xzz, t);
-        P[1] = {fmaf(9.0f, h.xz, e), fmaf(-9.0f, h.xz, e), fmaf(-4.5f, h.xzz, t)};
+        const f2 t = mul2(k2(3.0f), make_float2(h.jx, h.jy)), h3 = make_float2(h.xzz, h.yzz),
+                 h2 = make_float2(h.xz, h.yz);
+        const f2 e = fma2(k2(9.0f), h3, t);
+        P[1] = {fma2(k2(9.0f), h2, e), fma2(k2(-9.0f), h2, e), fma2(k2(-4.5f), h3, t)};
     }
     {
-        const float t = 3.0f * h.jy, e = fmaf(9.0f, h.yzz, t);
-        P[2] = {fmaf(9.0f, h.yz, e), fmaf(-9.0f, h.yz, e), fmaf(-4.5f, h.yzz, t)};
+        const f2 t = mul2(k2(1.5f), make_float2(h.xx, h.yy)), q = make_float2(h.xxz, h.yyz);
+        P[2] = {fma2(k2(4.5f), q, t), fma2(k2(-4.5f), q, t), t};
     }
     {
-        const float t = 1.5f * h.xx;
-        P[3] = {fmaf(4.5f, h.xxz, t), fmaf(-4.5f, h.xxz, t), t};
-    }
-    {
-        const float t = 1.5f * h.yy;
-        P[4] = {fmaf(4.5f, h.yyz, t), fmaf(-4.5f, h.yyz, t), t};
-    }
-    {
-        const float t = 9.0f * h.xy;
-        P[5] = {fmaf(27.0f, h.xyz, t), fmaf(-27.0f, h.xyz, t), t};
-    }
-    {
-        const float t = 4.5f * h.xxy;
-        P[6] = {t, t, t};
-    }
-    {
-        const float t = 4.5f * h.xyy;
-        P[7] = {t, t, t};
+        const f2 t = mul2(k2(4.5f), make_float2(h.xxy, h.xyy));
+        P[3] = {t, t, t};
     }
 }
 
@@ -226,8 +236,8 @@ struct Kernel {
 
     static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
                                                       const T* __restrict__ src, T* __restrict__ dst, float* ysm,
-                                                      char* pfb, float* corr, int j, float (&ppOld)[8],
-                                                      const float (&cOld)[8], float (&cNew)[8]) {
+                                                      char* pfb, float* corr, int j, f2 (&ppOld)[4],
+                                                      const f2 (&cOld)[4], f2 (&cNew)[4]) {
         const int zs = c.z0 - 1 + j;
         bool inflow_ghost;
         const int zl = plane_of(zs, g, c.zper, inflow_ghost);
@@ -241,7 +251,7 @@ struct Kernel {
         const T* v1 = reinterpret_cast<const T*>(pb + NT * PF::B01 + c.tid * PF::B01);
         const T* v2 = reinterpret_cast<const T*>(pb + 2 * NT * PF::B01 + c.tid * PF::B2);
         // ---- source plane: moments -> Hermite coefficients -> z populations ----
-        Pops P[8];
+        Pops2 P[4];
         {
             float m[NFIELDS];
             NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
@@ -263,22 +273,23 @@ struct Kernel {
             float* sb = ysm + (j & 1) * (YBUF / sizeof(float));
             float4* sv = reinterpret_cast<float4*>(sb);
             float* ss = sb + 4 * YV * NT;
-            // ---- z moments of plane z = zs - 1 ------------------------------
-            float Z[8][3];
+            // ---- z moments of plane z = zs - 1 (group pairs) ------------------
+            f2 Z[4][3];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float L = ppOld[k], R = P[k].pm;
-                Z[k][2] = L + R;
-                Z[k][1] = L - R;
-                Z[k][0] = fmaf(4.0f, cOld[k], Z[k][2]);
+            for (int i = 0; i < 4; ++i) {
+                Z[i][2] = add2(ppOld[i], P[i].pm);
+                Z[i][1] = sub2(ppOld[i], P[i].pm);
+                Z[i][0] = fma2(k2(4.0f), cOld[i], Z[i][2]);
             }
             // ---- y pass: groups jj = 3 k1 + r over k2 -----------------------
+            // group g of the z pass sits in pair G(g) = {0:(0,x) 1:(1,x) 2:(1,y)
+            // 3:(2,x) 4:(2,y) 5:(0,y) 6:(3,x) 7:(3,y)}
             Pops Q[9];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                Q[0 + r] = pops3(Z[0][r], Z[2][r], Z[4][r]);  // k1 = 0: k2 = 0, 1, 2
-                Q[3 + r] = pops3(Z[1][r], Z[5][r], Z[7][r]);  // k1 = 1
-                Q[6 + r] = pops2(Z[3][r], Z[6][r]);           // k1 = 2
+                Q[0 + r] = pops3(Z[0][r].x, Z[1][r].y, Z[2][r].y);  // k1 = 0: k2 = 0, 1, 2 (groups 0, 2, 4)
+                Q[3 + r] = pops3(Z[1][r].x, Z[0][r].y, Z[3][r].y);  // k1 = 1 (groups 1, 5, 7)
+                Q[6 + r] = pops2(Z[2][r].x, Z[3][r].x);             // k1 = 2 (groups 3, 6)
             }
             if (uni(c.zero_row)) {
                 // ghost row beyond a bounce-back wall: the entering deviation is zero
@@ -288,66 +299,64 @@ struct Kernel {
                 ss[c.tid] = 0.0f;
                 ss[NT + c.tid] = 0.0f;
             } else {
-                sv[0 * NT + c.tid] = make_float4(Q[0].pp, Q[1].pp, Q[2].pp, Q[3].pp);
-                sv[1 * NT + c.tid] = make_float4(Q[4].pp, Q[5].pp, Q[6].pp, Q[7].pp);
-                sv[2 * NT + c.tid] = make_float4(Q[0].pm, Q[1].pm, Q[2].pm, Q[3].pm);
-                sv[3 * NT + c.tid] = make_float4(Q[4].pm, Q[5].pm, Q[6].pm, Q[7].pm);
+                // slot order 0 1 3 4 | 6 7 2 5: the (r = 0, r = 1) pair of each k1 is adjacent
+                sv[0 * NT + c.tid] = make_float4(Q[0].pp, Q[1].pp, Q[3].pp, Q[4].pp);
+                sv[1 * NT + c.tid] = make_float4(Q[6].pp, Q[7].pp, Q[2].pp, Q[5].pp);
+                sv[2 * NT + c.tid] = make_float4(Q[0].pm, Q[1].pm, Q[3].pm, Q[4].pm);
+                sv[3 * NT + c.tid] = make_float4(Q[6].pm, Q[7].pm, Q[2].pm, Q[5].pm);
                 ss[c.tid] = Q[8].pp;
                 ss[NT + c.tid] = Q[8].pm;
             }
             __syncthreads();
             // halo and ghost rows only feed the y exchange (warp-uniform)
             if (uni(c.out_row)) {
-                float L[9], R[9];
+                // L / R: (r = 0, r = 1) pairs per k1 and the r = 2 scalars
+                f2 LA[3], RA[3];
+                float Ls[3], Rs[3];
                 {
                     const float4 l0 = sv[0 * NT + c.offLv], l1 = sv[1 * NT + c.offLv];
                     const float4 r0 = sv[2 * NT + c.offRv], r1 = sv[3 * NT + c.offRv];
-                    L[0] = l0.x; L[1] = l0.y; L[2] = l0.z; L[3] = l0.w;
-                    L[4] = l1.x; L[5] = l1.y; L[6] = l1.z; L[7] = l1.w;
-                    R[0] = r0.x; R[1] = r0.y; R[2] = r0.z; R[3] = r0.w;
-                    R[4] = r1.x; R[5] = r1.y; R[6] = r1.z; R[7] = r1.w;
-                    L[8] = ss[c.offLs];
-                    R[8] = ss[NT + c.offRs];
+                    LA[0] = make_float2(l0.x, l0.y); LA[1] = make_float2(l0.z, l0.w); LA[2] = make_float2(l1.x, l1.y);
+                    RA[0] = make_float2(r0.x, r0.y); RA[1] = make_float2(r0.z, r0.w); RA[2] = make_float2(r1.x, r1.y);
+                    Ls[0] = l1.z; Ls[1] = l1.w; Ls[2] = ss[c.offLs];
+                    Rs[0] = r1.z; Rs[1] = r1.w; Rs[2] = ss[NT + c.offRs];
                 }
-                // Y[k1][q][r] for (q, r) in {(0,0),(1,0),(2,0),(0,1),(1,1),(0,2)}
-                float Y[3][6];
+                // y moments in x-pass pair layout: Y03 = (q,r) groups (0,0) and (0,1),
+                // Y14 = (1,0) and (1,1), Y25 = (2,0) and (0,2)
+                f2 Y03[3], Y14[3], Y25[3];
 #pragma unroll
                 for (int k1 = 0; k1 < 3; ++k1) {
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        const int jj = 3 * k1 + r;
-                        const float sLR = L[jj] + R[jj];
-                        if (r == 0) {
-                            Y[k1][0] = fmaf(4.0f, Q[jj].c, sLR);  // q = 0
-                            Y[k1][1] = L[jj] - R[jj];              // q = 1
-                            Y[k1][2] = sLR;                        // q = 2
-                        } else if (r == 1) {
-                            Y[k1][3] = fmaf(4.0f, Q[jj].c, sLR);  // (q, r) = (0, 1)
-                            Y[k1][4] = L[jj] - R[jj];              // (1, 1)
-                        } else {
-                            Y[k1][5] = fmaf(4.0f, Q[jj].c, sLR);  // (0, 2)
-                        }
-                    }
+                    const f2 cc = make_float2(Q[3 * k1].c, Q[3 * k1 + 1].c);
+                    const f2 sLR = add2(LA[k1], RA[k1]);
+                    Y03[k1] = fma2(k2(4.0f), cc, sLR);
+                    Y14[k1] = sub2(LA[k1], RA[k1]);
+                    Y25[k1] = make_float2(LA[k1].x + RA[k1].x, fmaf(4.0f, Q[3 * k1 + 2].c, Ls[k1] + Rs[k1]));
                 }
-                // ---- x pass: groups (q, r) over k1 --------------------------
-                float Mo[6][3];
+                // ---- x pass: pairs of (q, r) groups over k1 ----------------------
+                f2 M0[3], M1[2], M2;
 #pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                    const Pops X = pops3(Y[0][k], Y[1][k], Y[2][k]);
-                    float Lx = __shfl_up_sync(0xffffffffu, X.pp, 1);
-                    float Rx = __shfl_down_sync(0xffffffffu, X.pm, 1);
+                for (int k = 0; k < 3; ++k) {
+                    const f2 a0 = k == 0 ? Y03[0] : (k == 1 ? Y14[0] : Y25[0]);
+                    const f2 a1 = k == 0 ? Y03[1] : (k == 1 ? Y14[1] : Y25[1]);
+                    const f2 a2 = k == 0 ? Y03[2] : (k == 1 ? Y14[2] : Y25[2]);
+                    const Pops2 X = pops3(a0, a1, a2);
+                    f2 Lx, Rx;
+                    Lx.x = __shfl_up_sync(0xffffffffu, X.pp.x, 1);
+                    Lx.y = __shfl_up_sync(0xffffffffu, X.pp.y, 1);
+                    Rx.x = __shfl_down_sync(0xffffffffu, X.pm.x, 1);
+                    Rx.y = __shfl_down_sync(0xffffffffu, X.pm.y, 1);
                     if (XFREE) {
                         if (c.xlo_mirror) Lx = X.pm;
                         if (c.xhi_mirror) Rx = X.pp;
                     }
-                    const float sLR = Lx + Rx;
-                    Mo[k][0] = fmaf(4.0f, X.c, sLR);
-                    Mo[k][1] = Lx - Rx;
-                    Mo[k][2] = sLR;
+                    const f2 sLR = add2(Lx, Rx);
+                    M0[k] = fma2(k2(4.0f), X.c, sLR);
+                    if (k < 2) M1[k] = sub2(Lx, Rx);
+                    if (k == 0) M2 = sLR;
                 }
-                float D0 = Mo[0][0];
-                float J[3] = {Mo[0][1], Mo[1][0], Mo[3][0]};
-                float S[6] = {Mo[0][2], Mo[2][0], Mo[5][0], Mo[1][1], Mo[3][1], Mo[4][0]};
+                float D0 = M0[0].x;
+                float J[3] = {M1[0].x, M0[1].x, M0[0].y};
+                float S[6] = {M2.x, M0[2].x, M0[2].y, M1[1].x, M1[0].y, M0[1].y};
                 // ---- halfway bounce-back on the wall-adjacent rows ----------
                 // The ghost row next to the wall computed the correction for
                 // this plane one march step earlier (see bounce_back_correction).
@@ -355,13 +364,10 @@ struct Kernel {
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
                         if (!uni(side == 0 ? c.row_lo : c.row_hi)) continue;
-                        const float* cb = corr + (((j + 1) & 1) * 2 + side) * NCORR * 32 + c.lane;
-                        D0 += cb[0 * 32];
-                        J[0] += cb[1 * 32];
-                        J[1] += cb[2 * 32];
-                        J[2] += cb[3 * 32];
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) S[k] += cb[(4 + k) * 32];
+                        const float* cb = corr + ((((j + 1) & 1) * 2 + side) * 32 + c.lane) * NCORR;
+                        const float4 b4 = *reinterpret_cast<const float4*>(cb);
+                        const float2 b2 = *reinterpret_cast<const float2*>(cb + 4);
+                        add_wall_moments(side == 0 ? 1.0f : -1.0f, b4.x, b4.y, b4.z, b4.w, b2.x, b2.y, D0, J, S);
                     }
                 }
                 float out[NFIELDS];
@@ -372,9 +378,9 @@ struct Kernel {
         }
         // ---- advance the z window --------------------------------------------
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            ppOld[k] = P[k].pp;
-            cNew[k] = P[k].c;
+        for (int i = 0; i < 4; ++i) {
+            ppOld[i] = P[i].pp;
+            cNew[i] = P[i].c;
         }
         if (uni(c.zero_row) && zs >= c.z0 && zs < c.z1) {
             // The ghost thread's column is clamped onto the wall-adjacent node,
@@ -384,7 +390,7 @@ struct Kernel {
             float F0, F1, F2;
             load_force(p, g, idx, F0, F1, F2);
             bounce_back_correction(m, F0, F1, F2, p.omega1, c.y < 0 ? 1.0f : -1.0f,
-                                   corr + ((j & 1) * 2 + (c.y < 0 ? 0 : 1)) * NCORR * 32 + c.lane);
+                                   corr + (((j & 1) * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
         }
     }
 
@@ -394,8 +400,8 @@ struct Kernel {
     // need only the y-contractions B_kx,kz = A_kx0kz + phi_1(-s) A_kx1kz +
     // 2 A_kx2kz of the post-collision modes at the leaving direction -s, and
     // the 1-D sums 6 (order 0), 2 (c phi_1) and 2 A_0 + 4 A_2 (c^2).
-    // s = +1 for the wall below the node, -1 for the wall above.  Writes the
-    // 216-scaled additions to D0, J, S (stride 32 floats).
+    // s = +1 for the wall below the node, -1 for the wall above.  Writes
+    // B00, B10, B01, B20, B02, B11 (one float4 and one float2).
     static __device__ __forceinline__ void bounce_back_correction(const float m[NFIELDS], float F0, float F1, float F2,
                                                                   float omega1, float s, float* out) {
         float Ao[NMODES];
@@ -406,17 +412,25 @@ struct Kernel {
         const float B20 = fmaf(-s, Ao[M210], Ao[M200]);
         const float B02 = fmaf(-s, Ao[M012], Ao[M002]);
         const float B11 = fmaf(-s, Ao[M111], Ao[M101]);
-        const float b36 = 36.0f * B00, b12 = 12.0f * B00, s12 = -12.0f * s;
-        out[0 * 32] = b36;                      // D0
-        out[1 * 32] = -12.0f * B10;             // J_x
-        out[2 * 32] = s * b36;                  // J_y
-        out[3 * 32] = -12.0f * B01;             // J_z
-        out[4 * 32] = fmaf(24.0f, B20, b12);    // S_xx
-        out[5 * 32] = b36;                      // S_yy
-        out[6 * 32] = fmaf(24.0f, B02, b12);    // S_zz
-        out[7 * 32] = s12 * B10;                // S_xy
-        out[8 * 32] = 4.0f * B11;               // S_xz
-        out[9 * 32] = s12 * B01;                // S_yz
+        *reinterpret_cast<float4*>(out) = make_float4(B00, B10, B01, B20);
+        *reinterpret_cast<float2*>(out + 4) = make_float2(B02, B11);
+    }
+
+    // 216-scaled moment sums of the reversed wall populations (entering y
+    // direction s) added to D0, J, S.
+    static __device__ __forceinline__ void add_wall_moments(float s, float B00, float B10, float B01, float B20,
+                                                            float B02, float B11, float& D0, float J[3], float S[6]) {
+        const float b36 = 36.0f * B00, s12 = -12.0f * s;
+        D0 += b36;
+        J[0] = fmaf(-12.0f, B10, J[0]);
+        J[1] = fmaf(s, b36, J[1]);
+        J[2] = fmaf(-12.0f, B01, J[2]);
+        S[0] = fmaf(12.0f, B00, fmaf(24.0f, B20, S[0]));
+        S[1] += b36;
+        S[2] = fmaf(12.0f, B00, fmaf(24.0f, B02, S[2]));
+        S[3] = fmaf(s12, B10, S[3]);
+        S[4] = fmaf(4.0f, B11, S[4]);
+        S[5] = fmaf(s12, B01, S[5]);
     }
 };
 
@@ -464,9 +478,9 @@ __global__ void __launch_bounds__(NT, 1)
     c.np = c.z1 - c.z0 + 2;
 
     K::prefetch(c, g, src, pfb, 0);
-    float ppA[8], ppB[8], cA[8], cB[8];
+    f2 ppA[4], ppB[4], cA[4], cB[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) ppA[k] = ppB[k] = cA[k] = cB[k] = 0.0f;
+    for (int i = 0; i < 4; ++i) ppA[i] = ppB[i] = cA[i] = cB[i] = k2(0.0f);
     // The window rotates by swapping roles between two register sets, so the
     // march advances two planes per loop trip without register copies.
     for (int j = 0; j < c.np; j += 2) {
