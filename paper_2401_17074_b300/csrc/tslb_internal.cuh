@@ -75,7 +75,7 @@ struct Physics {
 // ---- storage ----------------------------------------------------------------
 // One moment buffer holds three arrays of small vectors, one entry per stored
 // (interior) node, x fastest:
-//     V0 = (rho - 1, u_x, u_y, u_z)        at element 0
+//     V0 = (u_x, u_y, u_z, rho - 1)        at element 0
 //     V1 = (Pi_xx, Pi_yy, Pi_zz, Pi_xy)    at element 4 * fs
 //     V2 = (Pi_xz, Pi_yz)                  at element 8 * fs
 // (fs = node count padded to 128; 10 * fs elements per buffer).  FP32 storage
@@ -112,21 +112,22 @@ struct NodeIO {
         const uint2 a = __ldg(reinterpret_cast<const uint2*>(b) + n);
         const uint2 c = __ldg(reinterpret_cast<const uint2*>(b + 4 * fs) + n);
         const unsigned d = __ldg(reinterpret_cast<const unsigned*>(b + 8 * fs) + n);
-        float2 t = unpack(a.x);
-        m[F_DRHO] = t.x;
-        m[F_UX] = t.y * p.s_u;
+        const float2 su = make_float2(p.s_u, p.s_u), sp = make_float2(p.s_pi, p.s_pi);
+        float2 t = __fmul2_rn(unpack(a.x), su);
+        m[F_UX] = t.x;
+        m[F_UY] = t.y;
         t = unpack(a.y);
-        m[F_UY] = t.x * p.s_u;
-        m[F_UZ] = t.y * p.s_u;
-        t = unpack(c.x);
-        m[F_PXX] = t.x * p.s_pi;
-        m[F_PYY] = t.y * p.s_pi;
-        t = unpack(c.y);
-        m[F_PZZ] = t.x * p.s_pi;
-        m[F_PXY] = t.y * p.s_pi;
-        t = unpack(d);
-        m[F_PXZ] = t.x * p.s_pi;
-        m[F_PYZ] = t.y * p.s_pi;
+        m[F_UZ] = t.x * p.s_u;
+        m[F_DRHO] = t.y;
+        t = __fmul2_rn(unpack(c.x), sp);
+        m[F_PXX] = t.x;
+        m[F_PYY] = t.y;
+        t = __fmul2_rn(unpack(c.y), sp);
+        m[F_PZZ] = t.x;
+        m[F_PXY] = t.y;
+        t = __fmul2_rn(unpack(d), sp);
+        m[F_PXZ] = t.x;
+        m[F_PYZ] = t.y;
     }
     // Decode one node held as V0 / V1 / V2 vectors at v0, v1, v2 (shared memory).
     static __device__ __forceinline__ void decode_smem(const T* v0, const T* v1, const T* v2, const Physics& p,
@@ -134,26 +135,27 @@ struct NodeIO {
         const uint2 a = *reinterpret_cast<const uint2*>(v0);
         const uint2 c = *reinterpret_cast<const uint2*>(v1);
         const unsigned d = *reinterpret_cast<const unsigned*>(v2);
-        float2 t = unpack(a.x);
-        m[F_DRHO] = t.x;
-        m[F_UX] = t.y * p.s_u;
+        const float2 su = make_float2(p.s_u, p.s_u), sp = make_float2(p.s_pi, p.s_pi);
+        float2 t = __fmul2_rn(unpack(a.x), su);
+        m[F_UX] = t.x;
+        m[F_UY] = t.y;
         t = unpack(a.y);
-        m[F_UY] = t.x * p.s_u;
-        m[F_UZ] = t.y * p.s_u;
-        t = unpack(c.x);
-        m[F_PXX] = t.x * p.s_pi;
-        m[F_PYY] = t.y * p.s_pi;
-        t = unpack(c.y);
-        m[F_PZZ] = t.x * p.s_pi;
-        m[F_PXY] = t.y * p.s_pi;
-        t = unpack(d);
-        m[F_PXZ] = t.x * p.s_pi;
-        m[F_PYZ] = t.y * p.s_pi;
+        m[F_UZ] = t.x * p.s_u;
+        m[F_DRHO] = t.y;
+        t = __fmul2_rn(unpack(c.x), sp);
+        m[F_PXX] = t.x;
+        m[F_PYY] = t.y;
+        t = __fmul2_rn(unpack(c.y), sp);
+        m[F_PZZ] = t.x;
+        m[F_PXY] = t.y;
+        t = __fmul2_rn(unpack(d), sp);
+        m[F_PXZ] = t.x;
+        m[F_PYZ] = t.y;
     }
     static __device__ __forceinline__ void store(T* __restrict__ b, long long fs, long long n, const Physics& p,
                                                  const float m[NFIELDS]) {
         const float iu = p.inv_s_u, ip = p.inv_s_pi;
-        reinterpret_cast<uint2*>(b)[n] = make_uint2(pack(m[F_DRHO], m[F_UX] * iu), pack(m[F_UY] * iu, m[F_UZ] * iu));
+        reinterpret_cast<uint2*>(b)[n] = make_uint2(pack(m[F_UX] * iu, m[F_UY] * iu), pack(m[F_UZ] * iu, m[F_DRHO]));
         reinterpret_cast<uint2*>(b + 4 * fs)[n] =
             make_uint2(pack(m[F_PXX] * ip, m[F_PYY] * ip), pack(m[F_PZZ] * ip, m[F_PXY] * ip));
         reinterpret_cast<unsigned*>(b + 8 * fs)[n] = pack(m[F_PXZ] * ip, m[F_PYZ] * ip);
@@ -167,10 +169,10 @@ struct NodeIO<CodecF32> {
         const float4 a = __ldg(reinterpret_cast<const float4*>(b) + n);
         const float4 c = __ldg(reinterpret_cast<const float4*>(b + 4 * fs) + n);
         const float2 d = __ldg(reinterpret_cast<const float2*>(b + 8 * fs) + n);
-        m[F_DRHO] = a.x;
-        m[F_UX] = a.y;
-        m[F_UY] = a.z;
-        m[F_UZ] = a.w;
+        m[F_UX] = a.x;
+        m[F_UY] = a.y;
+        m[F_UZ] = a.z;
+        m[F_DRHO] = a.w;
         m[F_PXX] = c.x;
         m[F_PYY] = c.y;
         m[F_PZZ] = c.z;
@@ -183,10 +185,10 @@ struct NodeIO<CodecF32> {
         const float4 a = *reinterpret_cast<const float4*>(v0);
         const float4 c = *reinterpret_cast<const float4*>(v1);
         const float2 d = *reinterpret_cast<const float2*>(v2);
-        m[F_DRHO] = a.x;
-        m[F_UX] = a.y;
-        m[F_UY] = a.z;
-        m[F_UZ] = a.w;
+        m[F_UX] = a.x;
+        m[F_UY] = a.y;
+        m[F_UZ] = a.z;
+        m[F_DRHO] = a.w;
         m[F_PXX] = c.x;
         m[F_PYY] = c.y;
         m[F_PZZ] = c.z;
@@ -196,7 +198,7 @@ struct NodeIO<CodecF32> {
     }
     static __device__ __forceinline__ void store(float* __restrict__ b, long long fs, long long n, const Physics&,
                                                  const float m[NFIELDS]) {
-        reinterpret_cast<float4*>(b)[n] = make_float4(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ]);
+        reinterpret_cast<float4*>(b)[n] = make_float4(m[F_UX], m[F_UY], m[F_UZ], m[F_DRHO]);
         reinterpret_cast<float4*>(b + 4 * fs)[n] = make_float4(m[F_PXX], m[F_PYY], m[F_PZZ], m[F_PXY]);
         reinterpret_cast<float2*>(b + 8 * fs)[n] = make_float2(m[F_PXZ], m[F_PYZ]);
     }

@@ -156,13 +156,65 @@ __device__ __forceinline__ Herm hermite(float drho, float ux, float uy, float uz
     return h;
 }
 
+// Hermite coefficients in the pair layout of the z pass: scalars drho, h_zz,
+// h_xy, j_z, h_xyz and pairs (j_x, j_y), (h_xzz, h_yzz), (h_xz, h_yz),
+// (h_xx, h_yy), (h_xxz, h_yyz), (h_xxy, h_xyy).
+struct HermP {
+    float drho, zz, xy, jz, xyz;
+    f2 jxy, h3zz, h2z, h2d, h3z, h3y;
+};
+__device__ __forceinline__ HermP to_pairs(const Herm& h) {
+    HermP q;
+    q.drho = h.drho; q.zz = h.zz; q.xy = h.xy; q.jz = h.jz; q.xyz = h.xyz;
+    q.jxy = make_float2(h.jx, h.jy);
+    q.h3zz = make_float2(h.xzz, h.yzz);
+    q.h2z = make_float2(h.xz, h.yz);
+    q.h2d = make_float2(h.xx, h.yy);
+    q.h3z = make_float2(h.xxz, h.yyz);
+    q.h3y = make_float2(h.xxy, h.xyy);
+    return q;
+}
+// Same coefficients where the non-equilibrium velocity is u itself (every
+// stored node): with P = (1 - omega) Pi and t_ab = h2_ab + P_ab (= rho u_a u_b
+// + 2 P_ab), the third-order terms are h3_aab = u_a t_ab + u_b P_aa and
+// h3_xyz = rho u_x u_y u_z + u_x P_yz + u_y P_xz + u_z P_xy.  The x and y
+// components run as pairs.
+__device__ __forceinline__ HermP hermite_p(float drho, float ux, float uy, float uz, const float pi[6], float Fx,
+                                           float Fy, float Fz, float omega1) {
+    HermP q;
+    const float rho = 1.0f + drho;
+    const f2 rho2 = k2(rho), w2 = k2(omega1);
+    const f2 Pd = mul2(w2, make_float2(pi[0], pi[1]));   // (P_xx, P_yy)
+    const f2 Pzy = mul2(w2, make_float2(pi[2], pi[3]));  // (P_zz, P_xy)
+    const f2 Pq = mul2(w2, make_float2(pi[4], pi[5]));   // (P_xz, P_yz)
+    const f2 uxy = make_float2(ux, uy), uz2 = k2(uz);
+    const f2 ruxy = mul2(rho2, uxy);
+    const float ruz = rho * uz;
+    q.drho = drho;
+    q.jxy = fma2(rho2, make_float2(Fx, Fy), ruxy);
+    q.jz = fmaf(rho, Fz, ruz);
+    q.h2d = fma2(ruxy, uxy, Pd);
+    q.zz = fmaf(ruz, uz, Pzy.x);
+    const f2 qz = mul2(ruxy, uz2);  // (rho u_x u_z, rho u_y u_z)
+    const float qxy = ruxy.x * uy;
+    q.h2z = add2(qz, Pq);
+    q.xy = qxy + Pzy.y;
+    const f2 tz = add2(q.h2z, Pq);
+    const float txy = q.xy + Pzy.y;
+    q.h3zz = fma2(uz2, tz, mul2(uxy, k2(Pzy.x)));  // (h_xzz, h_yzz)
+    q.h3z = fma2(uxy, tz, mul2(uz2, Pd));          // (h_xxz, h_yyz)
+    q.h3y = make_float2(fmaf(ux, txy, uy * Pd.x), fmaf(uy, txy, ux * Pd.y));
+    q.xyz = fmaf(qxy, uz, fmaf(ux, Pq.y, fmaf(uy, Pq.x, uz * Pzy.y)));
+    return q;
+}
+
 // z populations of the eight (k1, k2) groups, modes
 //   (000, 001, 002) = (drho, 3 j_z, 1.5 h_zz),  (100, 101, 102) = (3 j_x, 9 h_xz, 4.5 h_xzz),
 //   (010, 011, 012) = (3 j_y, 9 h_yz, 4.5 h_yzz), (200, 201) = (1.5 h_xx, 4.5 h_xxz),
 //   (020, 021) = (1.5 h_yy, 4.5 h_yyz), (110, 111) = (9 h_xy, 27 h_xyz), 210 = 4.5 h_xxy,
 //   120 = 4.5 h_xyy, with the scale factors folded into the multiply-adds.
 // Pairs of groups in the z pass: G0 = (0, 5), G1 = (1, 2), G2 = (3, 4), G3 = (6, 7).
-__device__ __forceinline__ void zpops(const Herm& h, Pops2 P[4]) {
+__device__ __forceinline__ void zpops(const HermP& h, Pops2 P[4]) {
     {
         const f2 e = make_float2(fmaf(3.0f, h.zz, h.drho), 9.0f * h.xy);
         const f2 q = make_float2(h.jz, h.xyz);
@@ -170,17 +222,16 @@ __device__ __forceinline__ void zpops(const Herm& h, Pops2 P[4]) {
                 make_float2(fmaf(-1.5f, h.zz, h.drho), e.y)};
     }
     {
-        const f2 t = mul2(k2(3.0f), make_float2(h.jx, h.jy)), h3 = make_float2(h.xzz, h.yzz),
-                 h2 = make_float2(h.xz, h.yz);
+        const f2 t = mul2(k2(3.0f), h.jxy), h3 = h.h3zz, h2 = h.h2z;
         const f2 e = fma2(k2(9.0f), h3, t);
         P[1] = {fma2(k2(9.0f), h2, e), fma2(k2(-9.0f), h2, e), fma2(k2(-4.5f), h3, t)};
     }
     {
-        const f2 t = mul2(k2(1.5f), make_float2(h.xx, h.yy)), q = make_float2(h.xxz, h.yyz);
+        const f2 t = mul2(k2(1.5f), h.h2d), q = h.h3z;
         P[2] = {fma2(k2(4.5f), q, t), fma2(k2(-4.5f), q, t), t};
     }
     {
-        const f2 t = mul2(k2(4.5f), make_float2(h.xxy, h.xyy));
+        const f2 t = mul2(k2(4.5f), h.h3y);
         P[3] = {t, t, t};
     }
 }
@@ -221,32 +272,42 @@ struct Kernel {
     // receives c of zs.
     typedef Prefetch<(int)sizeof(T)> PF;
 
-    // Start the copies of march plane j's moments into prefetch buffer j & 1.
-    static __device__ __forceinline__ void prefetch(const Ctx& c, const Geometry& g, const T* __restrict__ src,
-                                                    char* pfb, int j) {
-        bool ig;
-        const int zl = plane_of(c.z0 - 1 + j, g, c.zper, ig);
+    // Start the copies of stored plane zl's moments (march plane j, PAR = j & 1)
+    // into prefetch buffer PAR.
+    template <int PAR>
+    static __device__ __forceinline__ void prefetch_plane(const Ctx& c, const Geometry& g, const T* __restrict__ src,
+                                                          char* pfb, int zl) {
         const unsigned n = c.col + c.plane * (unsigned)zl;
-        char* b = pfb + (j & 1) * PF::BUF;
+        char* b = pfb + PAR * PF::BUF;
         cp_async<PF::B01>(smem_u32(b + c.tid * PF::B01), src + (size_t)n * 4);
         cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * g.fstride + (size_t)n * 4);
         cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * g.fstride + (size_t)n * 2);
         cp_async_commit();
     }
+    template <int PAR>
+    static __device__ __forceinline__ void prefetch(const Ctx& c, const Geometry& g, const T* __restrict__ src,
+                                                    char* pfb, int j) {
+        bool ig;
+        prefetch_plane<PAR>(c, g, src, pfb, plane_of(c.z0 - 1 + j, g, c.zper, ig));
+    }
 
+    // STEADY: 2 <= j <= np - 3, so the plane and the next one are stored
+    // interior planes inside the chunk (no wrap, no ghost, exchange active).
+    template <int PAR, bool STEADY>
     static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
                                                       const T* __restrict__ src, T* __restrict__ dst, float* ysm,
                                                       char* pfb, float* corr, int j, f2 (&ppOld)[4],
                                                       const f2 (&cOld)[4], f2 (&cNew)[4]) {
         const int zs = c.z0 - 1 + j;
-        bool inflow_ghost;
-        const int zl = plane_of(zs, g, c.zper, inflow_ghost);
+        bool inflow_ghost = false;
+        const int zl = STEADY ? zs : plane_of(zs, g, c.zper, inflow_ghost);
         const unsigned idx = c.col + c.plane * (unsigned)zl;
         // next plane's copies go out before this plane's are consumed
-        if (zs < c.z1) prefetch(c, g, src, pfb, j + 1);
+        if (STEADY) prefetch_plane<PAR ^ 1>(c, g, src, pfb, zs + 1);
+        else if (zs < c.z1) prefetch<PAR ^ 1>(c, g, src, pfb, j + 1);
         else cp_async_commit();
         cp_async_wait_prev();
-        const char* pb = pfb + (j & 1) * PF::BUF;
+        const char* pb = pfb + PAR * PF::BUF;
         const T* v0 = reinterpret_cast<const T*>(pb + c.tid * PF::B01);
         const T* v1 = reinterpret_cast<const T*>(pb + NT * PF::B01 + c.tid * PF::B01);
         const T* v2 = reinterpret_cast<const T*>(pb + 2 * NT * PF::B01 + c.tid * PF::B2);
@@ -255,22 +316,21 @@ struct Kernel {
         {
             float m[NFIELDS];
             NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
-            Herm h;
-            if (inflow_ghost) {
+            HermP h;
+            if (!STEADY && inflow_ghost) {
                 const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
-                h = hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
-                            p.omega1);
+                h = to_pairs(hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
+                                     p.omega1));
             } else {
                 float F0, F1, F2;
                 load_force(p, g, idx, F0, F1, F2);
-                h = hermite(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
-                            p.omega1);
+                h = hermite_p(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, p.omega1);
             }
             zpops(h, P);
         }
 
-        if (zs >= c.z0 + 1) {
-            float* sb = ysm + (j & 1) * (YBUF / sizeof(float));
+        if (STEADY || zs >= c.z0 + 1) {
+            float* sb = ysm + PAR * (YBUF / sizeof(float));
             float4* sv = reinterpret_cast<float4*>(sb);
             float* ss = sb + 4 * YV * NT;
             // ---- z moments of plane z = zs - 1 (group pairs) ------------------
@@ -364,7 +424,7 @@ struct Kernel {
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
                         if (!uni(side == 0 ? c.row_lo : c.row_hi)) continue;
-                        const float* cb = corr + ((((j + 1) & 1) * 2 + side) * 32 + c.lane) * NCORR;
+                        const float* cb = corr + (((PAR ^ 1) * 2 + side) * 32 + c.lane) * NCORR;
                         const float4 b4 = *reinterpret_cast<const float4*>(cb);
                         const float2 b2 = *reinterpret_cast<const float2*>(cb + 4);
                         add_wall_moments(side == 0 ? 1.0f : -1.0f, b4.x, b4.y, b4.z, b4.w, b2.x, b2.y, D0, J, S);
@@ -382,7 +442,7 @@ struct Kernel {
             ppOld[i] = P[i].pp;
             cNew[i] = P[i].c;
         }
-        if (uni(c.zero_row) && zs >= c.z0 && zs < c.z1) {
+        if (uni(c.zero_row) && (STEADY || (zs >= c.z0 && zs < c.z1))) {
             // The ghost thread's column is clamped onto the wall-adjacent node,
             // so its prefetch slots hold that node's moments at plane zs.
             float m[NFIELDS];
@@ -390,7 +450,7 @@ struct Kernel {
             float F0, F1, F2;
             load_force(p, g, idx, F0, F1, F2);
             bounce_back_correction(m, F0, F1, F2, p.omega1, c.y < 0 ? 1.0f : -1.0f,
-                                   corr + (((j & 1) * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
+                                   corr + ((PAR * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
         }
     }
 
@@ -477,15 +537,24 @@ __global__ void __launch_bounds__(NT, 1)
     c.z1 = min(c.z0 + zchunk, g.nz);
     c.np = c.z1 - c.z0 + 2;
 
-    K::prefetch(c, g, src, pfb, 0);
+    K::template prefetch<0>(c, g, src, pfb, 0);
     f2 ppA[4], ppB[4], cA[4], cB[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) ppA[i] = ppB[i] = cA[i] = cB[i] = k2(0.0f);
     // The window rotates by swapping roles between two register sets, so the
     // march advances two planes per loop trip without register copies.
-    for (int j = 0; j < c.np; j += 2) {
-        K::plane_step(c, g, p, src, dst, ysm, pfb, corr, j, ppA, cA, cB);
-        if (j + 1 < c.np) K::plane_step(c, g, p, src, dst, ysm, pfb, corr, j + 1, ppB, cB, cA);
+    // Planes 0 and 1 (ghost / wrap, no exchange yet) and the last two or three
+    // take the general path; the steady loop in between has none of its tests.
+    K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, 0, ppA, cA, cB);
+    K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, 1, ppB, cB, cA);
+    int j = 2;
+    for (; j + 1 <= c.np - 3; j += 2) {
+        K::template plane_step<0, true>(c, g, p, src, dst, ysm, pfb, corr, j, ppA, cA, cB);
+        K::template plane_step<1, true>(c, g, p, src, dst, ysm, pfb, corr, j + 1, ppB, cB, cA);
+    }
+    for (; j < c.np; j += 2) {
+        K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, j, ppA, cA, cB);
+        if (j + 1 < c.np) K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, j + 1, ppB, cB, cA);
     }
 }
 
