@@ -30,7 +30,11 @@
 // its own shared-memory slots (three cp.async vector copies, L1-cached so the
 // halo re-reads of neighbouring tiles hit), reads them back when the plane
 // comes up, and stores its node's new moments with three vector stores; the
-// y exchange moves four values per shared-memory access.
+// y exchange moves four values per shared-memory access.  The exchange is
+// synchronised row to row (each warp row waits only for the rows above and
+// below, through shared-memory mbarriers) rather than by a CTA barrier, so
+// warps drift out of lockstep and the FP-heavy and shared-memory-heavy
+// phases of different rows overlap.
 //
 // Faces: periodic axes wrap; a free-slip face mirrors the 1-D pass (the
 // population entering from the wall side is the node's own population leaving
@@ -72,8 +76,10 @@ struct Prefetch {
 // y-contracted mode sums per lane, padded to eight floats).
 constexpr int NCORR = 8;
 constexpr size_t CORRBUF = sizeof(float) * 2 * 2 * NCORR * 32;
+// Exchange mbarriers: [WROWS rows][2 buffers].
+constexpr size_t BARBUF = sizeof(uint64_t) * WROWS * 2;
 template <int E>
-constexpr size_t smem_bytes() { return 2 * YBUF + 2 * Prefetch<E>::BUF + CORRBUF; }
+constexpr size_t smem_bytes() { return 2 * YBUF + 2 * Prefetch<E>::BUF + CORRBUF + BARBUF; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 template <int BYTES>
@@ -82,6 +88,47 @@ __device__ __forceinline__ void cp_async(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Row-to-row synchronisation of the y exchange (one mbarrier per row and
+// exchange buffer, arrival count 1): a row arrives (release) after writing its
+// slots and waits (acquire) only for the rows above and below.  A row can be
+// at most one exchange ahead of its neighbours, so a phase parity identifies
+// the exchange unambiguously; the write-after-read on a buffer reused two
+// planes later is ordered by the neighbours' arrivals in between, which
+// follow their reads.  The bounce-back correction handed from the ghost row
+// to the wall row is ordered the same way.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after about 2^31 SM clocks, records bit 2 in the
+// device status word and stops waiting for the rest of the launch.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* err, bool& dead) {
+    if (dead) return;
+    if (mbar_try_wait(bar, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) {
+            if (err) atomicOr(err, 2);
+            dead = true;
+            return;
+        }
+    }
+}
 
 // 1-D populations of a pass: p+, p- and c = a0 - a2 (p0 = 4 c).
 struct Pops {
@@ -296,7 +343,8 @@ struct Kernel {
     template <int PAR, bool STEADY>
     static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
                                                       const T* __restrict__ src, T* __restrict__ dst, float* ysm,
-                                                      char* pfb, float* corr, int j, f2 (&ppOld)[4],
+                                                      char* pfb, float* corr, uint64_t* bars, bool& dead, int j,
+                                                      f2 (&ppOld)[4],
                                                       const f2 (&cOld)[4], f2 (&cNew)[4]) {
         const int zs = c.z0 - 1 + j;
         bool inflow_ghost = false;
@@ -367,7 +415,13 @@ struct Kernel {
                 ss[c.tid] = Q[8].pp;
                 ss[NT + c.tid] = Q[8].pm;
             }
-            __syncthreads();
+            __syncwarp();
+            if (c.lane == 0) mbar_arrive(&bars[c.warp * 2 + PAR]);
+            {
+                const unsigned par = (unsigned)((j - 2) >> 1) & 1u;  // phase of this buffer's (j-2)/2-th use
+                if (c.warp > 0) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
+                if (c.warp < WROWS - 1) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
+            }
             // halo and ghost rows only feed the y exchange (warp-uniform)
             if (uni(c.out_row)) {
                 // L / R: (r = 0, r = 1) pairs per k1 and the r = 2 scalars
@@ -502,6 +556,10 @@ __global__ void __launch_bounds__(NT, 1)
     extern __shared__ __align__(16) float ysm[];  // [2][YBUF] y exchange, then [2][PF::BUF] plane prefetch
     char* pfb = reinterpret_cast<char*>(ysm) + 2 * YBUF;
     float* corr = reinterpret_cast<float*>(pfb + 2 * K::PF::BUF);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(corr) + CORRBUF);
+    if (threadIdx.x < WROWS * 2) mbar_init(&bars[threadIdx.x], 1);
+    __syncthreads();
+    bool dead = false;
 
     Ctx c;
     c.tid = threadIdx.x;
@@ -545,16 +603,16 @@ __global__ void __launch_bounds__(NT, 1)
     // march advances two planes per loop trip without register copies.
     // Planes 0 and 1 (ghost / wrap, no exchange yet) and the last two or three
     // take the general path; the steady loop in between has none of its tests.
-    K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, 0, ppA, cA, cB);
-    K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, 1, ppB, cB, cA);
+    K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, 0, ppA, cA, cB);
+    K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, 1, ppB, cB, cA);
     int j = 2;
     for (; j + 1 <= c.np - 3; j += 2) {
-        K::template plane_step<0, true>(c, g, p, src, dst, ysm, pfb, corr, j, ppA, cA, cB);
-        K::template plane_step<1, true>(c, g, p, src, dst, ysm, pfb, corr, j + 1, ppB, cB, cA);
+        K::template plane_step<0, true>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j, ppA, cA, cB);
+        K::template plane_step<1, true>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j + 1, ppB, cB, cA);
     }
     for (; j < c.np; j += 2) {
-        K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, j, ppA, cA, cB);
-        if (j + 1 < c.np) K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, j + 1, ppB, cB, cA);
+        K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j, ppA, cA, cB);
+        if (j + 1 < c.np) K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j + 1, ppB, cB, cA);
     }
 }
 
