@@ -30,6 +30,14 @@ bool inject_alloc_fault() {
     return f && std::strcmp(f, "alloc") == 0;
 }
 
+// TSLB_FAULT=exchange makes one warp row of the factored step withhold its
+// y-exchange arrival, so that its neighbours' bounded waits run out (about a
+// second) and the step reports the device status word.
+bool inject_exchange_fault() {
+    const char* f = std::getenv("TSLB_FAULT");
+    return f && std::strcmp(f, "exchange") == 0;
+}
+
 cudaError_t dev_alloc(void** p, size_t bytes) {
     if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
     return cudaMalloc(p, bytes);
@@ -90,6 +98,7 @@ Physics make_physics(const tslb_s* h) {
     p.in_seed = h->inflow.seed;
     p.t = h->t;
     p.err = h->dev_err;
+    p.drop_row = inject_exchange_fault() ? 5 : -1;
     if (h->precision == TSLB_FP32) {
         p.s_u = p.s_pi = p.inv_s_u = p.inv_s_pi = 1.0f;
     } else {

@@ -68,6 +68,7 @@ struct Physics {
     unsigned long long in_seed;
     long long t;           // step index of the state being read
     int* err;              // device status word (nonzero: a kernel gave up a bounded wait)
+    int drop_row;          // test hook: warp row of the factored step that withholds its exchange arrival (-1: none)
     // storage scales (16-bit codecs): value = stored * scale
     float s_u, s_pi, inv_s_u, inv_s_pi;
 };

@@ -416,7 +416,7 @@ struct Kernel {
                 ss[NT + c.tid] = Q[8].pm;
             }
             __syncwarp();
-            if (c.lane == 0) mbar_arrive(&bars[c.warp * 2 + PAR]);
+            if (c.lane == 0 && c.warp != p.drop_row) mbar_arrive(&bars[c.warp * 2 + PAR]);
             {
                 const unsigned par = (unsigned)((j - 2) >> 1) & 1u;  // phase of this buffer's (j-2)/2-th use
                 if (c.warp > 0) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);

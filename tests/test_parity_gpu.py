@@ -186,6 +186,32 @@ def test_alloc_fault_injection(cuda_ok, monkeypatch):
     assert ei.value.code == T.TSLB_ERR_ALLOC
 
 
+def test_lost_exchange_arrival_is_reported(cuda_ok, monkeypatch):
+    """One warp row of the factored step withholds its y-exchange arrival
+    (TSLB_FAULT=exchange): its neighbours' bounded waits run out after about a
+    second, the device status word makes the step report an error, and the
+    context stays usable for the next steps."""
+    dims = (60, 40, 6)
+    state = W.random_state(dims, seed=32)
+    s = T.Solver(dims, 0.6, kernel=T.KERNEL_FACTORED)
+    s.init_moments(*state)
+    monkeypatch.setenv("TSLB_FAULT", "exchange")
+    s.step(1)
+    with pytest.raises(T.TslbError, match="bounded device wait"):
+        s.synchronize()
+    monkeypatch.delenv("TSLB_FAULT")
+    s.init_moments(*state)
+    s.step(2)
+    got = stack(*s.get_moments())
+    s.close()
+    ref = T.Solver(dims, 0.6, kernel=T.KERNEL_FACTORED)
+    ref.init_moments(*state)
+    ref.step(2)
+    want = stack(*ref.get_moments())
+    ref.close()
+    assert np.array_equal(got, want)
+
+
 def test_unstable_reported_by_diagnostics(cuda_ok):
     dims = (6, 6, 6)
     s = T.Solver(dims, 0.6)
