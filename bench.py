@@ -216,6 +216,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(ms, dist, device="cuda"):
+    """The slowest rank's timed region (every rank receives it); ms unchanged on one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank, world_size, steps, ms):
+    """Whole-job throughput: node updates of all replicas over the slowest rank's time."""
+    return nodes_per_rank * world_size * steps / (ms * 1e-3) / 1e6
+
+
 def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, dist, clocks=None, keep=False):
     from paper_2401_17074_b300 import workloads as W
     s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], precision=PREC_CODE[precision],
@@ -236,9 +251,7 @@ def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, 
     ms = ev0.elapsed_time(ev1)
     ck = clocks.stop() if clocks else None
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist)
         dist.barrier()
     d, code = s.diagnostics()
     nodes = s.interior_nodes()
@@ -339,8 +352,7 @@ def main():
     ms, nodes, diag, code, ck, ref_final = time_device(T, torch, prm, state, args.precision, kernel, args.steps,
                                                        args.warmup, stream, dist, clocks,
                                                        keep=not args.no_variants and rank == 0)
-    total_nodes = nodes * ws
-    value = total_nodes * args.steps / (ms * 1e-3) / 1e6
+    value = job_mlups(nodes, ws, args.steps, ms)
     launch_s = ms * 1e-3 / args.steps
     bpn = BYTES_PER_NODE[args.precision]
     achieved = bpn * nodes / launch_s / 1e9
@@ -356,7 +368,7 @@ def main():
             msv, nv, dv, cv, _, fin = time_device(T, torch, prm, state, prec, kernel, args.steps, args.warmup,
                                                   stream, dist, keep=ref_final is not None)
             ls = msv * 1e-3 / args.steps
-            variants[prec] = {"value": nv * ws * args.steps / (msv * 1e-3) / 1e6, "unit": "MLUPS",
+            variants[prec] = {"value": job_mlups(nv, ws, args.steps, msv), "unit": "MLUPS",
                               "roofline_frac": BYTES_PER_NODE[prec] * nv / ls / 1e9 / hbm,
                               "bytes_per_node": BYTES_PER_NODE[prec], "stable": cv == T.TSLB_OK}
             if fin is not None:
