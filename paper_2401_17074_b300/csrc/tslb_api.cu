@@ -107,6 +107,8 @@ Physics make_physics(const tslb_s* h) {
         p.inv_s_u = (float)(1.0 / h->u_ref);
         p.inv_s_pi = (float)(1.0 / h->pi_ref);
     }
+    p.omega1_pi = (float)((1.0 - h->omega) * (double)p.s_pi);
+    p.pi_store = (float)((double)p.inv_s_pi / 216.0);
     return p;
 }
 

@@ -71,6 +71,9 @@ struct Physics {
     int drop_row;          // test hook: warp row of the factored step that withholds its exchange arrival (-1: none)
     // storage scales (16-bit codecs): value = stored * scale
     float s_u, s_pi, inv_s_u, inv_s_pi;
+    // (1 - omega) * s_pi, applied to Pi decoded without its storage scale, and
+    // inv_s_pi / 216, the factor from the 216-scaled sums to stored Pi
+    float omega1_pi, pi_store;
 };
 
 // ---- storage ----------------------------------------------------------------
@@ -153,6 +156,36 @@ struct NodeIO {
         m[F_PXZ] = t.x;
         m[F_PYZ] = t.y;
     }
+    // Same as decode_smem with Pi left in storage units (Pi / pi_ref).
+    static __device__ __forceinline__ void decode_smem_rawpi(const T* v0, const T* v1, const T* v2, const Physics& p,
+                                                             float m[NFIELDS]) {
+        const uint2 a = *reinterpret_cast<const uint2*>(v0);
+        const uint2 c = *reinterpret_cast<const uint2*>(v1);
+        const unsigned d = *reinterpret_cast<const unsigned*>(v2);
+        float2 t = __fmul2_rn(unpack(a.x), make_float2(p.s_u, p.s_u));
+        m[F_UX] = t.x;
+        m[F_UY] = t.y;
+        t = unpack(a.y);
+        m[F_UZ] = t.x * p.s_u;
+        m[F_DRHO] = t.y;
+        t = unpack(c.x);
+        m[F_PXX] = t.x;
+        m[F_PYY] = t.y;
+        t = unpack(c.y);
+        m[F_PZZ] = t.x;
+        m[F_PXY] = t.y;
+        t = unpack(d);
+        m[F_PXZ] = t.x;
+        m[F_PYZ] = t.y;
+    }
+    // Same as store with Pi already in storage units.
+    static __device__ __forceinline__ void store_rawpi(T* __restrict__ b, long long fs, long long n, const Physics& p,
+                                                       const float m[NFIELDS]) {
+        const float iu = p.inv_s_u;
+        reinterpret_cast<uint2*>(b)[n] = make_uint2(pack(m[F_UX] * iu, m[F_UY] * iu), pack(m[F_UZ] * iu, m[F_DRHO]));
+        reinterpret_cast<uint2*>(b + 4 * fs)[n] = make_uint2(pack(m[F_PXX], m[F_PYY]), pack(m[F_PZZ], m[F_PXY]));
+        reinterpret_cast<unsigned*>(b + 8 * fs)[n] = pack(m[F_PXZ], m[F_PYZ]);
+    }
     static __device__ __forceinline__ void store(T* __restrict__ b, long long fs, long long n, const Physics& p,
                                                  const float m[NFIELDS]) {
         const float iu = p.inv_s_u, ip = p.inv_s_pi;
@@ -196,6 +229,14 @@ struct NodeIO<CodecF32> {
         m[F_PXY] = c.w;
         m[F_PXZ] = d.x;
         m[F_PYZ] = d.y;
+    }
+    static __device__ __forceinline__ void decode_smem_rawpi(const float* v0, const float* v1, const float* v2,
+                                                             const Physics& p, float m[NFIELDS]) {
+        decode_smem(v0, v1, v2, p, m);
+    }
+    static __device__ __forceinline__ void store_rawpi(float* __restrict__ b, long long fs, long long n,
+                                                       const Physics& p, const float m[NFIELDS]) {
+        store(b, fs, n, p, m);
     }
     static __device__ __forceinline__ void store(float* __restrict__ b, long long fs, long long n, const Physics&,
                                                  const float m[NFIELDS]) {

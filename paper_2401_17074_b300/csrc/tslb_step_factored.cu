@@ -363,16 +363,16 @@ struct Kernel {
         Pops2 P[4];
         {
             float m[NFIELDS];
-            NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
+            NodeIO<Codec>::decode_smem_rawpi(v0, v1, v2, p, m);
             HermP h;
             if (!STEADY && inflow_ghost) {
                 const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
                 h = to_pairs(hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
-                                     p.omega1));
+                                     p.omega1_pi));
             } else {
                 float F0, F1, F2;
                 load_force(p, g, idx, F0, F1, F2);
-                h = hermite_p(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, p.omega1);
+                h = hermite_p(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, p.omega1_pi);
             }
             zpops(h, P);
         }
@@ -485,9 +485,27 @@ struct Kernel {
                     }
                 }
                 float out[NFIELDS];
-                finish_moments(D0, J, S, out);
+                if (sizeof(T) == 4) {
+                    finish_moments(D0, J, S, out);
+                } else {
+                    // 16-bit storage: Pi goes straight to storage units (the
+                    // 16-bit rounding dominates the single-multiply scaling)
+                    const float inv = rcp_refined(216.0f + D0);
+                    const float ux = J[0] * inv, uy = J[1] * inv, uz = J[2] * inv;
+                    const float d3 = D0 * (1.0f / 3.0f), ps = p.pi_store;
+                    out[F_DRHO] = div216(D0);
+                    out[F_UX] = ux;
+                    out[F_UY] = uy;
+                    out[F_UZ] = uz;
+                    out[F_PXX] = (S[0] - fmaf(J[0], ux, d3)) * ps;
+                    out[F_PYY] = (S[1] - fmaf(J[1], uy, d3)) * ps;
+                    out[F_PZZ] = (S[2] - fmaf(J[2], uz, d3)) * ps;
+                    out[F_PXY] = (S[3] - J[0] * uy) * ps;
+                    out[F_PXZ] = (S[4] - J[0] * uz) * ps;
+                    out[F_PYZ] = (S[5] - J[1] * uz) * ps;
+                }
                 const unsigned oidx = c.col + c.plane * (unsigned)(zs - 1);
-                if (c.store) NodeIO<Codec>::store(dst, g.fstride, oidx, p, out);
+                if (c.store) NodeIO<Codec>::store_rawpi(dst, g.fstride, oidx, p, out);
             }
         }
         // ---- advance the z window --------------------------------------------
@@ -500,10 +518,10 @@ struct Kernel {
             // The ghost thread's column is clamped onto the wall-adjacent node,
             // so its prefetch slots hold that node's moments at plane zs.
             float m[NFIELDS];
-            NodeIO<Codec>::decode_smem(v0, v1, v2, p, m);
+            NodeIO<Codec>::decode_smem_rawpi(v0, v1, v2, p, m);
             float F0, F1, F2;
             load_force(p, g, idx, F0, F1, F2);
-            bounce_back_correction(m, F0, F1, F2, p.omega1, c.y < 0 ? 1.0f : -1.0f,
+            bounce_back_correction(m, F0, F1, F2, p.omega1_pi, c.y < 0 ? 1.0f : -1.0f,
                                    corr + ((PAR * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
         }
     }
