@@ -590,7 +590,11 @@ __global__ void __launch_bounds__(NT, 1)
     c.ybb = g.bc[2] == TSLB_BC_BOUNCEBACK;
     const bool yfs = g.bc[2] == TSLB_BC_FREESLIP;
     c.zper = g.bc[4] == TSLB_BC_PERIODIC;
-    c.xl = XFREE ? min(max(c.x, 0), g.nx - 1) : (c.x + g.nx) % g.nx;
+    // Lanes outside the lattice read a wrapped column: on a free-slip x face
+    // their values are never used (the boundary lane takes its own mirrored
+    // population instead), and distinct columns keep the warp's copies free of
+    // repeated addresses, which the copy engine would serialise.
+    c.xl = (c.x + g.nx) % g.nx;
     c.yl = yper ? (c.y + g.ny) % g.ny : min(max(c.y, 0), g.ny - 1);
     c.col = (unsigned)c.xl + (unsigned)g.nx * (unsigned)c.yl;
     c.plane = (unsigned)g.plane;
