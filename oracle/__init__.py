@@ -50,6 +50,9 @@ def lib():
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_inflow_noise.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         L.orc_inflow_noise.restype = ctypes.c_double
+        L.orc_inflow_noise_gauss.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+        L.orc_inflow_noise_gauss.restype = ctypes.c_double
+        L.orc_set_sponge.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]
         L.orc_create.argtypes = [i64p, ctypes.c_double, dp, ip, i64p, dp, ctypes.c_uint64, ip]
         L.orc_create.restype = ctypes.c_void_p
         L.orc_destroy.argtypes = [ctypes.c_void_p]
@@ -124,29 +127,35 @@ def inflow_noise(seed, x, y, t):
     return lib().orc_inflow_noise(int(seed), int(x), int(y), int(t))
 
 
+def inflow_noise_gauss(seed, x, y, t):
+    return lib().orc_inflow_noise_gauss(int(seed), int(x), int(y), int(t))
+
+
 class OracleSim:
     """Population-based FP64 TSLB simulation on a full nx*ny*nz lattice.
 
     bc = (x-, x+, y-, y+, z-, z+) face codes.  A non-periodic face makes the
     outermost node layer a boundary layer (solid for BOUNCEBACK / FREESLIP,
     ghost for INFLOW / OUTFLOW); only interior nodes are updated.
-    inflow = dict(center2=(cx2, cy2), diameter=D, u_jet=U, noise_amp=a, seed=s[, origin=(ox, oy)]);
-    origin places this box inside a larger lattice for the nozzle mask and the
-    noise counter (a sub-box that reproduces part of a full-size run).
+    inflow = dict(center2=(cx2, cy2), diameter=D, u_jet=U, noise_amp=a, seed=s[, origin=(ox, oy)]
+    [, noise="uniform" | "gaussian"]); origin places this box inside a larger lattice for the nozzle
+    mask and the noise counter (a sub-box that reproduces part of a full-size run).
+    sponge = (W, K): viscosity raised over the last W layers towards z+ (jet exit).
     """
 
-    def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, inflow=None):
+    def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, inflow=None, sponge=None):
         self.dims = tuple(int(d) for d in dims)
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
         d = np.array(self.dims, dtype=np.int64)
         F = _f64(force)
         b = np.array(bc, dtype=np.int32)
-        ii = np.zeros(5, dtype=np.int64)
+        ii = np.zeros(6, dtype=np.int64)
         dd = np.zeros(2)
         seed = 0
         if inflow is not None:
             org = inflow.get("origin", (0, 0))
-            ii[:] = [inflow["center2"][0], inflow["center2"][1], inflow["diameter"], org[0], org[1]]
+            kind = {"uniform": 0, "gaussian": 1}[inflow.get("noise", "uniform")]
+            ii[:] = [inflow["center2"][0], inflow["center2"][1], inflow["diameter"], org[0], org[1], kind]
             dd[:] = [inflow["u_jet"], inflow["noise_amp"]]
             seed = int(inflow["seed"])
         st = ctypes.c_int(0)
@@ -156,6 +165,9 @@ class OracleSim:
                                    seed, ctypes.byref(st))
         if not self._h:
             raise ValueError("oracle rejected the configuration (status %d)" % st.value)
+        if sponge is not None:
+            if lib().orc_set_sponge(self._h, int(sponge[0]), float(sponge[1])) != 0:
+                raise ValueError("oracle rejected the sponge layer")
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -37,6 +37,17 @@
 //       velocity u_B for f^eq, and Pi^neq and u of x_F for the Hermite f^neq
 //       (Eq. neq_final: all a^n_neq evaluated at x_F).
 //   R7  the outflow ghost node (x,y,nz-1) takes the moments of (x,y,nz-2).
+//   R8  the jet's sponge layer (Sec. 3.2, viscosity raised towards the exit)
+//       is nu(z) = nu (1 + K ((z - z_s)/W)^3) for z > z_s = nz - W, with the
+//       exponent taken as +3 (the printed -3 diverges at z_s) and W = nz - z_s
+//       as the normalising length (the printed z_end is not defined); every
+//       node relaxes with omega(z) = 1 / (1/2 + nu(z)/cs^2) of its own z, ghost
+//       layers included.
+//   R9  "time-varying Gaussian noise" on the inflow: u_z = u_jet (1 + a xi),
+//       xi ~ N(0,1) drawn per column and step by the Box-Muller transform of
+//       the same Philox4x32-10 block as the uniform noise:
+//       u1 = ((r0 >> 8) + 1) 2^-24 in (0, 1], u2 = (r1 >> 8) 2^-24,
+//       xi = sqrt(-2 ln u1) cos(2 pi u2).
 //
 // Parity status: every function is pinned by the tests in tests/ (moment
 // identities, rest state, conservation, forcing, Taylor-Green and shear-wave
@@ -192,6 +203,20 @@ double inflow_noise(uint64_t seed, int64_t x, int64_t y, int64_t t) {
     return (double)(r[0] >> 8) * (1.0 / 8388608.0) - 1.0;
 }
 
+// Gaussian noise xi ~ N(0,1) for inflow column (x, y) at time step t (R9).
+double inflow_noise_gauss(uint64_t seed, int64_t x, int64_t y, int64_t t) {
+    uint32_t ctr[4] = {(uint32_t)x, (uint32_t)y, (uint32_t)t, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    philox4x32_10(ctr, key, r);
+    const double u1 = (double)((r[0] >> 8) + 1u) * (1.0 / 16777216.0);
+    const double u2 = (double)(r[1] >> 8) * (1.0 / 16777216.0);
+    const double two_pi = 6.283185307179586476925286766559;
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(two_pi * u2);
+}
+
+enum { NOISE_UNIFORM = 0, NOISE_GAUSSIAN = 1 };
+
 struct Inflow {
     int64_t center2[2];  // twice the nozzle centre (x, y), in node units
     int64_t diameter;    // nozzle diameter D in node units; inside <=> |2x-cx2|^2+|2y-cy2|^2 <= D^2
@@ -200,6 +225,7 @@ struct Inflow {
     uint64_t seed;
     int64_t origin[2];   // lattice coordinates of this box's node (0, 0) in a larger lattice
                          // (lets a sub-box reproduce the nozzle and noise of the full one)
+    int noise_kind;      // NOISE_UNIFORM (xi ~ U(-1,1)) or NOISE_GAUSSIAN (R9)
 };
 
 template <class T>
@@ -213,6 +239,18 @@ struct Sim {
     Inflow inflow;
     int64_t t;
     std::vector<T> f, fnew;  // [node][27]
+    int64_t sponge_w;        // sponge layer width W (0: none), R8
+    double sponge_k;         // sponge strength K
+
+    // Relaxation rate of a node at lattice z (R8).
+    double omega_at(int64_t z) const {
+        const int64_t zs = n[2] - sponge_w;
+        if (sponge_w <= 0 || z <= zs) return omega;
+        const double nu0 = CS2 * (1.0 / omega - 0.5);
+        const double r = (double)(z - zs) / (double)sponge_w;
+        const double nu = nu0 * (1.0 + sponge_k * r * r * r);
+        return 1.0 / (0.5 + nu / CS2);
+    }
 
     int64_t N() const { return n[0] * n[1] * n[2]; }
     int64_t idx(int64_t x, int64_t y, int64_t z) const { return x + n[0] * (y + n[1] * z); }
@@ -243,13 +281,15 @@ void source_post(const Sim<T>& s, int64_t x, int64_t y, int64_t z, T out[27]) {
         const int64_t X = x + s.inflow.origin[0], Y = y + s.inflow.origin[1];
         int64_t dx = 2 * X - s.inflow.center2[0], dy = 2 * Y - s.inflow.center2[1];
         if (dx * dx + dy * dy <= s.inflow.diameter * s.inflow.diameter) {
-            double xi = inflow_noise(s.inflow.seed, X, Y, s.t);
+            double xi = s.inflow.noise_kind == NOISE_GAUSSIAN ? inflow_noise_gauss(s.inflow.seed, X, Y, s.t)
+                                                               : inflow_noise(s.inflow.seed, X, Y, s.t);
             uB[2] = s.inflow.u_jet * (1.0 + s.inflow.noise_amp * xi);
         }
         T eq[27], neq[27];
         feq3(rho, uB, eq);     // imposed velocity, extrapolated density
         fneq3(pi, u, neq);     // Hermite f^neq from x_F (Eq. neq_final)
-        for (int i = 0; i < 27; ++i) out[i] = eq[i] + (1.0 - s.omega) * neq[i];
+        const double w = s.omega_at(z);
+        for (int i = 0; i < 27; ++i) out[i] = eq[i] + (1.0 - w) * neq[i];
         return;
     }
     int64_t zs = z;
@@ -257,7 +297,7 @@ void source_post(const Sim<T>& s, int64_t x, int64_t y, int64_t z, T out[27]) {
     int64_t node = s.idx(x, y, zs);
     node_moments(s, node, rho, u, pi);
     s.force_at(node, F);
-    post_collision(rho, u, pi, s.omega, F, out);
+    post_collision(rho, u, pi, s.omega_at(z), F, out);
 }
 
 // One push-form step (Eq. pushLB): every source emits its 27 post-collision
@@ -348,6 +388,8 @@ int validate_and_init(Sim<T>* s, const int64_t dims[3], double tau, const double
     std::memset(&s->inflow, 0, sizeof(Inflow));
     if (inflow) s->inflow = *inflow;
     s->t = 0;
+    s->sponge_w = 0;
+    s->sponge_k = 0.0;
     s->f.assign(s->N() * 27, T(0.0));
     s->fnew.assign(s->N() * 27, T(0.0));
     return 0;
@@ -428,6 +470,9 @@ void orc_moments(const double* f, double* rho, double* u, double* pi6) {
 }
 void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
 double orc_inflow_noise(uint64_t seed, int64_t x, int64_t y, int64_t t) { return inflow_noise(seed, x, y, t); }
+double orc_inflow_noise_gauss(uint64_t seed, int64_t x, int64_t y, int64_t t) {
+    return inflow_noise_gauss(seed, x, y, t);
+}
 
 // ---- real (FP64) simulation ------------------------------------------------
 void* orc_create(const int64_t* dims, double tau, const double* F, const int* bc, const int64_t* inflow_i,
@@ -438,6 +483,7 @@ void* orc_create(const int64_t* dims, double tau, const double* F, const int* bc
     if (inflow_i) {
         in.center2[0] = inflow_i[0]; in.center2[1] = inflow_i[1]; in.diameter = inflow_i[2];
         in.origin[0] = inflow_i[3]; in.origin[1] = inflow_i[4];
+        in.noise_kind = (int)inflow_i[5];
     }
     if (inflow_d) { in.u_jet = inflow_d[0]; in.noise_amp = inflow_d[1]; }
     in.seed = seed;
@@ -447,6 +493,14 @@ void* orc_create(const int64_t* dims, double tau, const double* F, const int* bc
     return s;
 }
 void orc_destroy(void* h) { delete static_cast<Sim<double>*>(h); }
+// Sponge layer of width W (0: none) and strength K along the z+ end (R8).
+int orc_set_sponge(void* h, int64_t width, double k) {
+    Sim<double>* s = static_cast<Sim<double>*>(h);
+    if (width < 0 || width >= s->n[2] || !(k >= 0.0)) return -1;
+    s->sponge_w = width;
+    s->sponge_k = k;
+    return 0;
+}
 int orc_init_moments(void* h, const double* rho, const double* u, const double* pi) {
     init_from_moments(static_cast<Sim<double>*>(h), rho, u, pi);
     return 0;

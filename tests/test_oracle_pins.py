@@ -394,6 +394,58 @@ def _energy_real(dims, tau, rho, u, pi, F, nsteps):
     return 0.5 * np.sum(r * (uu ** 2).sum(0))
 
 
+def test_gaussian_inflow_noise_statistics():
+    """Gaussian inflow noise (reading of the jet's "time-varying Gaussian noise",
+    Sec. 3.2): Box-Muller on the Philox block gives xi ~ N(0, 1) per column and
+    step, independent from one step to the next."""
+    nx, ny, nt = 200, 100, 10
+    xi = np.array([[oracle.inflow_noise_gauss(3, x, y, t) for t in range(nt)]
+                   for x in range(nx) for y in range(ny)])  # [column][t]
+    v = xi.reshape(-1)
+    n = v.size
+    assert abs(v.mean()) < 4.5 / math.sqrt(n)
+    assert abs(v.var() - 1.0) < 4.5 * math.sqrt(2.0 / n)
+    srt = np.sort(v)
+    cdf = 0.5 * (1.0 + np.array([math.erf(q / math.sqrt(2.0)) for q in srt]))
+    emp_hi = np.arange(1, n + 1) / n
+    emp_lo = np.arange(0, n) / n
+    ks = max(np.abs(emp_hi - cdf).max(), np.abs(emp_lo - cdf).max())
+    assert ks < 1.95 / math.sqrt(n)  # 99.9 % Kolmogorov-Smirnov bound
+    lag1 = np.corrcoef(xi[:, :-1].reshape(-1), xi[:, 1:].reshape(-1))[0, 1]
+    assert abs(lag1) < 4.5 / math.sqrt(xi[:, 1:].size)
+
+
+def test_sponge_layer_local_viscosity():
+    """Sponge layer (reading of Sec. 3.2): each plane relaxes with its own
+    nu(z) = nu (1 + K ((z - z_s)/W)^3) above z_s = nz - W; a z-uniform shear
+    wave then decays at nu(z) k^2 plane by plane (K small enough that the
+    momentum exchanged between planes stays below the tolerance)."""
+    dims, tau, width, K = (3, 32, 40), 0.6, 20, 1.0
+    nx, ny, nz = dims
+    rho, u, pi = W.shear_wave(dims, 1e-3, tau)
+    s = oracle.OracleSim(dims, tau, sponge=(width, K))
+    s.init_moments(rho, u, pi)
+    k = 2 * math.pi / ny
+    basis = np.sin(k * np.arange(ny))
+
+    def amps():
+        _, uu, _ = s.get_moments()
+        ux = uu[0].reshape(nz, ny, nx).mean(axis=2)
+        return ux @ basis / (basis @ basis)
+
+    s.step(5)  # the initial Pi follows the unsponged tau: let it relax
+    a0 = amps()
+    s.step(10)
+    rate = -np.log(amps() / a0) / 10.0
+    nu0 = CS2 * (tau - 0.5)
+    zs = nz - width
+    r = np.clip((np.arange(nz) - zs) / width, 0.0, None)
+    nu = nu0 * (1.0 + K * r ** 3)
+    for z in list(range(5, 16)) + list(range(zs + 5, nz - 4)):
+        assert abs(rate[z] / (nu[z] * k * k) - 1.0) < 0.02, (z, rate[z], nu[z] * k * k)
+    assert nu[nz - 5] > 1.4 * nu0  # the checked range does reach into the layer
+
+
 def test_complex_step_matches_central_differences():
     dims = (4, 4, 4)
     N = 64
