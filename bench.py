@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the paper-jet workload line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -269,6 +270,39 @@ def precision_errors(prm, ref, got):
             "pi_field": rel(got[2], ref[2])}
 
 
+def time_jet_paper(T, torch, stream, steps=200, warmup=20):
+    """The paper's jet set-up at its own size (440 x 440 x 600, periodic crossflow,
+    Gaussian inflow noise, sponge layer), from the paper's initial state (fluid at
+    rest), built on the device; FP32 storage, the default kernel."""
+    from paper_2401_17074_b300 import workloads as W
+    prm = W.jet_paper_params()
+    dims = prm["dims"]
+    N = dims[0] * dims[1] * dims[2]
+    s = T.Solver(dims, prm["tau"], force=prm["force"], bc=prm["bc"], inflow=prm["inflow"], sponge=prm["sponge"],
+                 stream=stream.cuda_stream)
+    rho = torch.ones(N, dtype=torch.float64, device="cuda")
+    zeros = torch.zeros((9, N), dtype=torch.float64, device="cuda")
+    s.init_moments(rho, zeros[0:3], zeros[3:9])
+    del rho, zeros
+    s.step(warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    d, code = s.diagnostics()
+    nodes = s.interior_nodes()
+    s.close()
+    torch.cuda.empty_cache()
+    return {"workload": "round jet %dx%dx%d (paper set-up): periodic x,y, NEE inflow with Gaussian noise, "
+                        "outflow, sponge width %d K=%g; fp32 storage" % (dims + prm["sponge"]),
+            "value": job_mlups(nodes, 1, steps, ms), "unit": "MLUPS", "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "interior_nodes": nodes, "max_speed": d["max_speed"], "status": code}
+
+
 def time_adjoint(T, torch, stream, n=128, nsteps=64, k=16, tau=0.52):
     """Forward (with checkpoints) and discrete adjoint of the force gradient on an n^3 periodic box."""
     from paper_2401_17074_b300 import workloads as W
@@ -382,6 +416,9 @@ def main():
     adj = None
     if not args.no_adjoint and rank == 0:
         adj = time_adjoint(T, torch, stream)
+    jet = None
+    if not args.no_extra and rank == 0:
+        jet = time_jet_paper(T, torch, stream)
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(prm, args.cpu_seconds)
@@ -404,6 +441,7 @@ def main():
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "adjoint": adj,
+            "workloads": {"jet_paper": jet} if jet else None,
             "clocks": ck,
             "diagnostics_after_timed": {"mass": diag["mass"], "max_speed": diag["max_speed"], "status": code},
         }

@@ -78,16 +78,26 @@ typedef enum tslb_kernel {
     TSLB_KERNEL_FACTORED = 2  /* sum-factorised, z-marching tiled kernel */
 } tslb_kernel;
 
+/* Inflow noise of the round jet (Sec. 3.2). */
+typedef enum tslb_noise {
+    TSLB_NOISE_UNIFORM = 0, /* xi uniform in [-1, 1): (r0 >> 8) 2^-23 - 1 */
+    TSLB_NOISE_GAUSSIAN = 1 /* xi ~ N(0, 1), the paper's "time-varying Gaussian noise": Box-Muller,
+                               xi = sqrt(-2 ln u1) cos(2 pi u2), u1 = ((r0 >> 8) + 1) 2^-24,
+                               u2 = (r1 >> 8) 2^-24 */
+} tslb_noise;
+
 /* Inflow nozzle of the round jet (Sec. 3.2): inside the disc
  * (2x - center2[0])^2 + (2y - center2[1])^2 <= diameter^2 the imposed velocity
- * is u_z = u_jet (1 + noise_amp * xi), xi uniform in [-1, 1) drawn per column
- * and per step from Philox4x32-10 keyed by `seed`; outside it is zero. */
+ * is u_z = u_jet (1 + noise_amp * xi), with xi drawn per column (x, y) and per
+ * step t from the Philox4x32-10 block of counter (x, y, t, 0) and key `seed`
+ * (r0, r1 its first two words) as `noise_kind` says; outside it is zero. */
 typedef struct tslb_inflow {
     int64_t center2[2];
     int64_t diameter;
     double u_jet;
     double noise_amp;
     uint64_t seed;
+    int noise_kind;       /* tslb_noise, default TSLB_NOISE_UNIFORM */
 } tslb_inflow;
 
 typedef struct tslb_options {
@@ -99,6 +109,15 @@ typedef struct tslb_options {
     int kernel;           /* tslb_kernel, default TSLB_KERNEL_AUTO */
     int checkpoint_every; /* >0: tslb_step records a moment checkpoint every k steps (adjoint) */
     tslb_inflow inflow;   /* used when bc[4] == TSLB_BC_INFLOW */
+    /* Sponge layer towards the z+ face (the jet's exit, Sec. 3.2): with
+     * W = sponge_width > 0 (default 0 = none) and z_s = nz - W, a node at
+     * lattice z > z_s relaxes with nu(z) = nu (1 + sponge_k ((z - z_s)/W)^3),
+     * nu = cs^2 (tau - 1/2), i.e. omega(z) = 1 / (1/2 + nu(z)/cs^2).  The
+     * paper prints the exponent as -3 (which diverges at z_s) and normalises by
+     * an undefined z_end; +3 and W are this library's reading.  Requires
+     * W < nz and sponge_k >= 0; not supported by tslb_adjoint_force_gradient. */
+    int sponge_width;
+    double sponge_k;
 } tslb_options;
 
 typedef struct tslb_diag {

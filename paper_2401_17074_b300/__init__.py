@@ -26,6 +26,7 @@ PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
 FP32, BF16, FP16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED = 0, 1, 2
+TSLB_NOISE_UNIFORM, TSLB_NOISE_GAUSSIAN = 0, 1
 
 EXPORTED = [
     "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_set_force_field", "tslb_step",
@@ -37,13 +38,14 @@ NOALLOC_MAX_NODES = 1 << 26
 
 class tslb_inflow(ctypes.Structure):
     _fields_ = [("center2", ctypes.c_int64 * 2), ("diameter", ctypes.c_int64), ("u_jet", ctypes.c_double),
-                ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64), ("noise_kind", ctypes.c_int)]
 
 
 class tslb_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("u_ref", ctypes.c_double), ("pi_ref", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("checkpoint_every", ctypes.c_int), ("inflow", tslb_inflow)]
+                ("checkpoint_every", ctypes.c_int), ("inflow", tslb_inflow), ("sponge_width", ctypes.c_int),
+                ("sponge_k", ctypes.c_double)]
 
 
 class tslb_diag(ctypes.Structure):
@@ -229,7 +231,9 @@ class Solver:
     """Owns one TSLB handle.  Arrays follow the C ABI layouts (full lattice, x fastest)."""
 
     def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05, pi_ref=1e-3,
-                 kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None):
+                 kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None, sponge=None):
+        """inflow: dict(center2, diameter, u_jet, noise_amp, seed[, noise="uniform" | "gaussian"]);
+        sponge: (width, K) viscosity layer towards the z+ face (tslb_options.sponge_width / sponge_k)."""
         o = tslb_options_default()
         o.precision = int(precision)
         o.u_ref = float(u_ref)
@@ -246,6 +250,11 @@ class Solver:
             o.inflow.u_jet = float(inflow["u_jet"])
             o.inflow.noise_amp = float(inflow["noise_amp"])
             o.inflow.seed = int(inflow["seed"])
+            o.inflow.noise_kind = {"uniform": TSLB_NOISE_UNIFORM,
+                                   "gaussian": TSLB_NOISE_GAUSSIAN}[inflow.get("noise", "uniform")]
+        if sponge is not None:
+            o.sponge_width = int(sponge[0])
+            o.sponge_k = float(sponge[1])
         self.dims = tuple(int(d) for d in dims)
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
         self._h = tslb_create(self.dims, tau, force, bc, o)

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "tslb_internal.cuh"
 
@@ -73,6 +74,7 @@ void release(tslb_s* h) {
     if (h->force_field) cudaFree(h->force_field);
     if (h->diag_part) cudaFree(h->diag_part);
     if (h->dev_err) cudaFree(h->dev_err);
+    if (h->omega1_z) cudaFree(h->omega1_z);
     if (h->diag_host) cudaFreeHost(h->diag_host);
     for (void* c : h->ckpts) cudaFree(c);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -96,6 +98,8 @@ Physics make_physics(const tslb_s* h) {
     p.in_u = (float)h->inflow.u_jet;
     p.in_amp = (float)h->inflow.noise_amp;
     p.in_seed = h->inflow.seed;
+    p.in_gauss = h->inflow.noise_kind == TSLB_NOISE_GAUSSIAN ? 1 : 0;
+    p.omega1_z = h->omega1_z;
     p.t = h->t;
     p.err = h->dev_err;
     p.drop_row = inject_exchange_fault() ? 5 : -1;
@@ -186,6 +190,10 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_INVALID, "unknown kernel choice");
     if (o.checkpoint_every < 0) return fail(nullptr, TSLB_ERR_INVALID, "checkpoint_every < 0");
     if (bz0 == TSLB_BC_INFLOW && o.inflow.diameter < 0) return fail(nullptr, TSLB_ERR_INVALID, "bad inflow diameter");
+    if (o.inflow.noise_kind != TSLB_NOISE_UNIFORM && o.inflow.noise_kind != TSLB_NOISE_GAUSSIAN)
+        return fail(nullptr, TSLB_ERR_INVALID, "unknown inflow noise kind");
+    if (o.sponge_width < 0 || o.sponge_width >= dims[2] || !(o.sponge_k >= 0.0) || !std::isfinite(o.sponge_k))
+        return fail(nullptr, TSLB_ERR_INVALID, "sponge layer needs 0 <= width < nz and K >= 0");
 
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -205,6 +213,8 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     h->kernel = o.kernel;
     h->checkpoint_every = o.checkpoint_every;
     h->inflow = o.inflow;
+    h->sponge_width = o.sponge_width;
+    h->sponge_k = o.sponge_k;
     h->elem = o.precision == TSLB_FP32 ? 4 : 2;
 
     tslb::Geometry& g = h->g;
@@ -252,6 +262,31 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         if (e != cudaSuccess) {
             release(h);
             return cuda_fail(nullptr, e, "cudaMemsetAsync");
+        }
+    }
+    if (h->sponge_width > 0) {
+        // (1 - omega) per full-lattice z: nu(z) = nu (1 + K ((z - z_s)/W)^3) above z_s = nz - W
+        const int64_t nzf = dims[2], W = h->sponge_width, zs = nzf - W;
+        const double nu0 = (tau - 0.5) / 3.0;
+        std::vector<float> tab((size_t)nzf);
+        for (int64_t z = 0; z < nzf; ++z) {
+            double nu = nu0;
+            if (z > zs) {
+                const double r = (double)(z - zs) / (double)W;
+                nu = nu0 * (1.0 + h->sponge_k * r * r * r);
+            }
+            tab[(size_t)z] = (float)(1.0 - 1.0 / (0.5 + 3.0 * nu));
+        }
+        e = dev_alloc((void**)&h->omega1_z, sizeof(float) * (size_t)nzf);
+        if (e != cudaSuccess) {
+            std::string m = std::string("device allocation of the sponge table failed: ") + cudaGetErrorString(e);
+            release(h);
+            return fail(nullptr, TSLB_ERR_ALLOC, m);
+        }
+        e = cudaMemcpy(h->omega1_z, tab.data(), sizeof(float) * (size_t)nzf, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            release(h);
+            return cuda_fail(nullptr, e, "sponge table copy");
         }
     }
     int sms = 148;
@@ -435,6 +470,7 @@ int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int wher
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (!dJdF) return fail(h, TSLB_ERR_INVALID, "null output");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    if (h->omega1_z) return fail(h, TSLB_ERR_UNSUPPORTED, "the adjoint does not support a sponge layer");
     cudaSetDevice(h->device);
     std::string msg;
     const int r = tslb::adjoint_force_gradient(h, nsteps, dJdF, where, &msg);

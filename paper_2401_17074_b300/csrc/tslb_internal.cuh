@@ -66,6 +66,7 @@ struct Physics {
     float in_u;
     float in_amp;
     unsigned long long in_seed;
+    int in_gauss;          // Gaussian (Box-Muller) instead of uniform inflow noise
     long long t;           // step index of the state being read
     int* err;              // device status word (nonzero: a kernel gave up a bounded wait)
     int drop_row;          // test hook: warp row of the factored step that withholds its exchange arrival (-1: none)
@@ -74,6 +75,8 @@ struct Physics {
     // (1 - omega) * s_pi, applied to Pi decoded without its storage scale, and
     // inv_s_pi / 216, the factor from the 216-scaled sums to stored Pi
     float omega1_pi, pi_store;
+    // sponge layer: (1 - omega) per full-lattice z, or nullptr (uniform omega)
+    const float* omega1_z;
 };
 
 // ---- storage ----------------------------------------------------------------
@@ -362,14 +365,35 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
     }
 }
 
-// Imposed inflow velocity u_z at lattice column (x, y) for step t.
+// (1 - omega) of a node at full-lattice z (the sponge layer's table when set).
+__device__ __forceinline__ float omega1_at(const Physics& p, int zfull) {
+    return p.omega1_z ? __ldg(p.omega1_z + zfull) : p.omega1;
+}
+
+// Imposed inflow velocity u_z at lattice column (x, y) for step t.  The draw
+// is kept out of line (it runs once per column of the inflow plane) and takes
+// its parameters by value, so it leaves the step kernels' register allocation
+// alone.
+static __device__ __noinline__ float inflow_uz_draw(long long x, long long y, long long c2x, long long c2y, long long d,
+                                             long long t, unsigned long long seed, float u_jet, float amp,
+                                             int gauss) {
+    const long long dx = 2 * x - c2x, dy = 2 * y - c2y;
+    if (dx * dx + dy * dy > d * d) return 0.0f;
+    uint32_t c[4] = {(uint32_t)x, (uint32_t)y, (uint32_t)t, 0u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    float xi;
+    if (gauss) {
+        // Box-Muller on the block's first two words: u1 in (0, 1], u2 in [0, 1)
+        const float u1 = (float)((c[0] >> 8) + 1u) * (1.0f / 16777216.0f);
+        const float u2 = (float)(c[1] >> 8) * (1.0f / 16777216.0f);
+        xi = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    } else {
+        xi = (float)(c[0] >> 8) * (1.0f / 8388608.0f) - 1.0f;
+    }
+    return u_jet * (1.0f + amp * xi);
+}
 __device__ __forceinline__ float inflow_uz(const Physics& p, long long x, long long y) {
-    const long long dx = 2 * x - p.in_c2[0], dy = 2 * y - p.in_c2[1];
-    if (dx * dx + dy * dy > p.in_d * p.in_d) return 0.0f;
-    uint32_t c[4] = {(uint32_t)x, (uint32_t)y, (uint32_t)p.t, 0u};
-    philox4x32_10(c, (uint32_t)p.in_seed, (uint32_t)(p.in_seed >> 32));
-    const float xi = (float)(c[0] >> 8) * (1.0f / 8388608.0f) - 1.0f;
-    return p.in_u * (1.0f + p.in_amp * xi);
+    return inflow_uz_draw(x, y, p.in_c2[0], p.in_c2[1], p.in_d, p.t, p.in_seed, p.in_u, p.in_amp, p.in_gauss);
 }
 
 }  // namespace tslb
@@ -391,6 +415,9 @@ struct tslb_s {
     int* dev_err = nullptr;  // device status word of the bounded waits
     int checkpoint_every = 0;
     tslb_inflow inflow{};
+    int sponge_width = 0;
+    double sponge_k = 0.0;
+    float* omega1_z = nullptr;  // sponge layer table, (1 - omega) per full-lattice z
     size_t elem = 4;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;

@@ -22,7 +22,7 @@ __device__ __forceinline__ void load_node(const typename Codec::T* __restrict__ 
 
 template <class Codec>
 __device__ __forceinline__ void node_modes(const typename Codec::T* __restrict__ src, const Geometry& g,
-                                           const Physics& p, long long idx, float A[NMODES]) {
+                                           const Physics& p, long long idx, int zfull, float A[NMODES]) {
     float m[NFIELDS];
     load_node<Codec>(src, g, p, idx, m);
     float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
@@ -31,7 +31,8 @@ __device__ __forceinline__ void node_modes(const typename Codec::T* __restrict__
         F1 = p.force[g.fstride + idx];
         F2 = p.force[2 * g.fstride + idx];
     }
-    post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, p.omega1, A);
+    post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
+               omega1_at(p, zfull), A);
 }
 
 template <class Codec>
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
 
     float D0 = 0.f, J[3] = {0.f, 0.f, 0.f}, S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float Aown[NMODES];
-    node_modes<Codec>(src, g, p, n, Aown);
+    node_modes<Codec>(src, g, p, n, own[2] + g.lo[2], Aown);
 
     for (int cz = -1; cz <= 1; ++cz)
         for (int cy = -1; cy <= 1; ++cy)
@@ -84,12 +85,13 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
                     const float uBz = inflow_uz(p, (long long)s[0] + g.lo[0], (long long)s[1] + g.lo[1]);
                     float A[NMODES];
                     post_modes(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
-                               p.omega1, A);
+                               omega1_at(p, 0), A);
                     gi = pop_dev216(A, c[0], c[1], c[2]);
                 } else {
                     const long long sidx = (long long)s[0] + (long long)g.nx * s[1] + g.plane * s[2];
                     float A[NMODES];
-                    node_modes<Codec>(src, g, p, sidx, A);
+                    // an outflow ghost relaxes with the omega of its own layer
+                    node_modes<Codec>(src, g, p, sidx, ghost == 2 ? ext[2] + g.lo[2] : s[2] + g.lo[2], A);
                     gi = pop_dev216(A, c[0], c[1], c[2]);
                 }
                 D0 += gi;

@@ -310,7 +310,7 @@ struct Ctx {
     int offLv, offRv, offLs, offRs;  // y-exchange read offsets (float4 / float units, relative to a slot base)
 };
 
-template <class Codec, bool XFREE>
+template <class Codec, bool XFREE, bool SPONGE>
 struct Kernel {
     typedef typename Codec::T T;
 
@@ -350,6 +350,10 @@ struct Kernel {
         bool inflow_ghost = false;
         const int zl = STEADY ? zs : plane_of(zs, g, c.zper, inflow_ghost);
         const unsigned idx = c.col + c.plane * (unsigned)zl;
+        // (1 - omega) s_pi of this source plane: uniform, or the sponge layer's
+        // value at the plane's lattice z (ghost planes included)
+        const float om_pi = SPONGE ? __ldg(p.omega1_z + ((!STEADY && c.zper) ? zl : zs + g.lo[2])) * p.s_pi
+                                   : p.omega1_pi;
         // next plane's copies go out before this plane's are consumed
         if (STEADY) prefetch_plane<PAR ^ 1>(c, g, src, pfb, zs + 1);
         else if (zs < c.z1) prefetch<PAR ^ 1>(c, g, src, pfb, j + 1);
@@ -368,11 +372,11 @@ struct Kernel {
             if (!STEADY && inflow_ghost) {
                 const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
                 h = to_pairs(hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
-                                     p.omega1_pi));
+                                     om_pi));
             } else {
                 float F0, F1, F2;
                 load_force(p, g, idx, F0, F1, F2);
-                h = hermite_p(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, p.omega1_pi);
+                h = hermite_p(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, om_pi);
             }
             zpops(h, P);
         }
@@ -521,7 +525,7 @@ struct Kernel {
             NodeIO<Codec>::decode_smem_rawpi(v0, v1, v2, p, m);
             float F0, F1, F2;
             load_force(p, g, idx, F0, F1, F2);
-            bounce_back_correction(m, F0, F1, F2, p.omega1_pi, c.y < 0 ? 1.0f : -1.0f,
+            bounce_back_correction(m, F0, F1, F2, om_pi, c.y < 0 ? 1.0f : -1.0f,
                                    corr + ((PAR * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
         }
     }
@@ -566,11 +570,11 @@ struct Kernel {
     }
 };
 
-template <class Codec, bool XFREE>
+template <class Codec, bool XFREE, bool SPONGE>
 __global__ void __launch_bounds__(NT, 1)
     step_factored_kernel(const typename Codec::T* __restrict__ src, typename Codec::T* __restrict__ dst, Geometry g,
                          Physics p, int zchunk) {
-    typedef Kernel<Codec, XFREE> K;
+    typedef Kernel<Codec, XFREE, SPONGE> K;
     extern __shared__ __align__(16) float ysm[];  // [2][YBUF] y exchange, then [2][PF::BUF] plane prefetch
     char* pfb = reinterpret_cast<char*>(ysm) + 2 * YBUF;
     float* corr = reinterpret_cast<float*>(pfb + 2 * K::PF::BUF);
@@ -638,9 +642,9 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
-template <class Codec, bool XFREE>
+template <class Codec, bool XFREE, bool SPONGE>
 cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    auto kern = step_factored_kernel<Codec, XFREE>;
+    auto kern = step_factored_kernel<Codec, XFREE, SPONGE>;
     static bool configured[64] = {};
     const int dev = h->device;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -678,8 +682,9 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
 
 template <class Codec>
 cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    if (h->g.bc[0] == TSLB_BC_FREESLIP) return launch_t<Codec, true>(h, src, dst, p);
-    return launch_t<Codec, false>(h, src, dst, p);
+    const bool xfree = h->g.bc[0] == TSLB_BC_FREESLIP, sponge = p.omega1_z != nullptr;
+    if (xfree) return sponge ? launch_t<Codec, true, true>(h, src, dst, p) : launch_t<Codec, true, false>(h, src, dst, p);
+    return sponge ? launch_t<Codec, false, true>(h, src, dst, p) : launch_t<Codec, false, false>(h, src, dst, p);
 }
 
 }  // namespace

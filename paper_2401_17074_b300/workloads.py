@@ -161,6 +161,22 @@ def jet_params(nx=256, ny=256, nz=640, D=20, u_jet=0.05, re=7000.0, noise_amp=0.
                 bc=(FREESLIP, FREESLIP, FREESLIP, FREESLIP, INFLOW, OUTFLOW), inflow=inflow, nu=nu)
 
 
+def jet_paper_params(nx=440, ny=440, nz=600, D=20, u_jet=0.05, re=7000.0, noise_amp=0.01, seed=3,
+                     sponge_width=50, sponge_k=1000.0):
+    """The paper's round-jet set-up (Sec. 3.2): 440 x 440 x 600, periodic crossflow
+    (x and y), Hermite-NEE inflow at z = 0 with a uniform profile plus
+    time-varying Gaussian noise, outflow at z = nz-1, and a sponge layer of
+    width 50 and strength K = 1000 before the exit.  tau from Re = U D / nu.
+    """
+    nu = u_jet * D / re
+    tau = 0.5 + nu / CS2
+    inflow = dict(center2=(nx - 1, ny - 1), diameter=D, u_jet=u_jet, noise_amp=noise_amp, seed=seed,
+                  noise="gaussian")
+    return dict(dims=(nx, ny, nz), tau=tau, force=(0.0, 0.0, 0.0),
+                bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC, INFLOW, OUTFLOW), inflow=inflow, nu=nu,
+                sponge=(sponge_width, sponge_k))
+
+
 # ---- adjoint box (128^3 periodic, divergence-free random velocity) ----------
 
 def divfree_random(n=128, u_rms=0.02, kmax=8, tau=0.52, seed=5):

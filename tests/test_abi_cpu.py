@@ -90,6 +90,20 @@ def test_bad_option_values_rejected():
     assert c == T.TSLB_ERR_INVALID
 
 
+def test_bad_sponge_and_noise_rejected():
+    for width, k in ((-1, 10.0), (8, 10.0), (3, -1.0), (3, float("nan"))):  # dims z = 8
+        o = T.tslb_options_default()
+        o.sponge_width = width
+        o.sponge_k = k
+        c, h = _create_code(opt=o)
+        assert c == T.TSLB_ERR_INVALID, (width, k)
+        assert not h.value
+    o = T.tslb_options_default()
+    o.inflow.noise_kind = 5
+    c, h = _create_code(opt=o)
+    assert c == T.TSLB_ERR_INVALID
+
+
 def test_null_handle_calls_fail_cleanly():
     L = T.load()
     assert L.tslb_step(None, 1) == T.TSLB_ERR_INVALID

@@ -20,8 +20,15 @@ NSTEPS = 2
 
 
 def _cut(arr, dims, xs, ys, zs):
-    """Full-lattice [..., N] array -> sub-box [..., n] over lattice index lists xs, ys, zs."""
+    """Full-lattice [..., N] array (numpy, or a CUDA tensor) -> numpy sub-box [..., n] over index lists xs, ys, zs."""
     nx, ny, nz = dims
+    if hasattr(arr, "is_cuda"):
+        import torch
+        dev = arr.device
+        a = arr.reshape(tuple(arr.shape[:-1]) + (nz, ny, nx))
+        a = a.index_select(-3, torch.as_tensor(zs, device=dev)).index_select(-2, torch.as_tensor(ys, device=dev))
+        a = a.index_select(-1, torch.as_tensor(xs, device=dev))
+        return a.reshape(tuple(arr.shape[:-1]) + (-1,)).cpu().numpy()
     a = arr.reshape(arr.shape[:-1] + (nz, ny, nx))
     a = a[..., zs, :, :][..., :, ys, :][..., :, :, xs]
     return np.ascontiguousarray(a.reshape(arr.shape[:-1] + (-1,)))
@@ -35,7 +42,7 @@ def _axis_range(c, n, periodic, R):
     return list(range(lo, hi + 1)), False
 
 
-def _compare_column(gpu, state_full, dims, tau, force, bc, col, inflow=None):
+def _compare_column(gpu, state_full, dims, tau, force, bc, col, inflow=None, sponge=None):
     """Run the oracle on the sub-box around column `col` and compare that column.
 
     col: dict with the two sampled coordinates (the third axis is kept whole).
@@ -64,7 +71,7 @@ def _compare_column(gpu, state_full, dims, tau, force, bc, col, inflow=None):
     if inflow is not None:
         sin = dict(inflow)
         sin["origin"] = (xs[0], ys[0])
-    o = oracle.OracleSim(sdims, tau, force=force, bc=tuple(sbc), inflow=sin)
+    o = oracle.OracleSim(sdims, tau, force=force, bc=tuple(sbc), inflow=sin, sponge=sponge)
     o.init_moments(*sub)
     o.step(NSTEPS)
     r, uu, pp = o.get_moments()
@@ -76,16 +83,13 @@ def _compare_column(gpu, state_full, dims, tau, force, bc, col, inflow=None):
     iy = ys.index(col[1]) if 1 in col else slice(None)
     iz = zs.index(col[2]) if 2 in col else slice(None)
     sel[iz, iy, ix] = True
-    # interior of the full lattice only
-    inner = np.ones((nz, ny, nx), bool)
-    if bc[0]:
-        inner[:, :, [0, nx - 1]] = False
-    if bc[2]:
-        inner[:, [0, ny - 1], :] = False
-    if bc[4]:
-        inner[[0, nz - 1], :, :] = False
-    inner_sub = _cut(inner.reshape(-1).astype(np.float64)[None], dims, xs, ys, zs)[0] > 0.5
-    m = sel.reshape(-1) & inner_sub
+    # interior of the full lattice only (per axis: not a boundary layer)
+    keep = []
+    for a, idx in enumerate((xs, ys, zs)):
+        n = dims[a]
+        keep.append(np.array([bc[2 * a] == 0 or 0 < i < n - 1 for i in idx]))
+    inner_sub = keep[2][:, None, None] & keep[1][None, :, None] & keep[0][None, None, :]
+    m = sel.reshape(-1) & inner_sub.reshape(-1)
     return got[:, m], ref[:, m]
 
 
@@ -166,4 +170,36 @@ def test_jet_full_size_sampled(cuda_ok):
             {0: 30, 1: 17}]
     pairs = [_compare_column(gpu, state, dims, prm["tau"], prm["force"], prm["bc"], c, inflow=prm["inflow"])
              for c in cols]
+    _check(pairs, 3e-6)
+
+
+@pytest.mark.gpu
+def test_paper_jet_full_size_sampled(cuda_ok):
+    """The paper's jet at its own size (Sec. 3.2: 440 x 440 x 600, periodic
+    crossflow, Gaussian inflow noise, sponge of width 50 with K = 1000).  The
+    state is drawn on the device from a seeded generator, so no full-lattice
+    host copy is made; sampled columns span every z, through the sponge."""
+    import torch
+    prm = W.jet_paper_params()
+    dims = prm["dims"]
+    N = dims[0] * dims[1] * dims[2]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(51)
+
+    def unif(shape, scale):
+        return (torch.rand(shape, generator=gen, device="cuda", dtype=torch.float64) * 2.0 - 1.0) * scale
+
+    rho = 1.0 + unif((N,), 0.002)
+    u = unif((3, N), 0.01)
+    pi = unif((6, N), 1e-4)
+    s = T.Solver(dims, prm["tau"], force=prm["force"], bc=prm["bc"], inflow=prm["inflow"], sponge=prm["sponge"])
+    s.init_moments(rho, u, pi)
+    s.step(NSTEPS)
+    out = torch.empty((10, N), dtype=torch.float64, device="cuda")
+    T.tslb_get_moments(s.handle, out[0], out[1:4], out[4:10], T.DEVICE)
+    s.close()
+    out[0] -= 1.0
+    cols = [{0: 219, 1: 219}, {0: 210, 1: 223}, {0: 0, 1: 0}, {0: 439, 1: 100}, {0: 30, 1: 17}, {0: 300, 1: 431}]
+    pairs = [_compare_column(out, (rho, u, pi), dims, prm["tau"], prm["force"], prm["bc"], c, inflow=prm["inflow"],
+                             sponge=prm["sponge"]) for c in cols]
     _check(pairs, 3e-6)

@@ -47,14 +47,14 @@ def rel_errors(gpu, ref, mask):
 
 
 def run_pair(dims, tau, state, nsteps, kernel, bc=(0,) * 6, force=(0.0, 0.0, 0.0), inflow=None, precision=T.FP32,
-             force_field=None):
-    o = oracle.OracleSim(dims, tau, force=force, bc=bc, inflow=inflow)
+             force_field=None, sponge=None):
+    o = oracle.OracleSim(dims, tau, force=force, bc=bc, inflow=inflow, sponge=sponge)
     o.init_moments(*state)
     if force_field is not None:
         o.set_force_field(force_field.astype(np.float64))
     o.step(nsteps)
     ref = stack(*o.get_moments())
-    s = T.Solver(dims, tau, force=force, bc=bc, kernel=kernel, inflow=inflow, precision=precision)
+    s = T.Solver(dims, tau, force=force, bc=bc, kernel=kernel, inflow=inflow, precision=precision, sponge=sponge)
     s.init_moments(*state)
     if force_field is not None:
         s.set_force_field(force_field.astype(np.float32))
@@ -155,6 +155,29 @@ def test_jet_faces_small(cuda_ok, kernel):
     state = W.random_state(dims, seed=25, drho=0.002, du=0.01, dpi=1e-4)
     errs, _, _ = run_pair(dims, 0.52, state, 20, kernel, bc=bc, inflow=inflow)
     assert_all_below(errs, 1e-5)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_paper_jet_faces_small(cuda_ok, kernel):
+    """The paper's jet faces (Sec. 3.2): periodic crossflow, Hermite-NEE inflow
+    with time-varying Gaussian noise, outflow, and a sponge layer (K = 1000)
+    over the last 10 layers, on a small box with a ragged x tile."""
+    dims = (34, 24, 40)
+    bc = (0, 0, 0, 0, 3, 4)
+    inflow = dict(center2=(33, 23), diameter=8, u_jet=0.05, noise_amp=0.01, seed=3, noise="gaussian")
+    state = W.random_state(dims, seed=28, drho=0.002, du=0.01, dpi=1e-4)
+    errs, _, _ = run_pair(dims, 0.52, state, 20, kernel, bc=bc, inflow=inflow, sponge=(10, 1000.0))
+    assert_all_below(errs, 1e-5)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_sponge_with_periodic_z(cuda_ok, kernel):
+    """Sponge table on a periodic axis: the plane wrap of the march reads the
+    table at the wrapped plane."""
+    dims = (12, 10, 16)
+    state = W.random_state(dims, seed=29, drho=0.002, du=0.01, dpi=1e-4)
+    errs, _, _ = run_pair(dims, 0.6, state, 6, kernel, sponge=(6, 5.0))
+    assert_all_below(errs, 3e-6)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
