@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tslb_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
+PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL = 0, 1, 2, 3, 4, 5
 
 _lib = None
 

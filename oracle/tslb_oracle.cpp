@@ -48,6 +48,13 @@
 //       the same Philox4x32-10 block as the uniform noise:
 //       u1 = ((r0 >> 8) + 1) 2^-24 in (0, 1], u2 = (r1 >> 8) 2^-24,
 //       xi = sqrt(-2 ln u1) cos(2 pi u2).
+//   R10 no-slip walls by the thread-safe non-equilibrium extrapolation
+//       (Sec. 2.3, Eq. neq_final with the imposed momentum u_B = 0): the wall
+//       sits on the boundary layer y = 0 (or ny-1), whose nodes emit
+//       f^eq(rho_F, 0) + (1-omega) Hermite f^neq(Pi^neq, u of x_F) with x_F the
+//       adjacent fluid node (rho_B extrapolated from x_F, no body force);
+//       populations streamed into the layer are dropped.  Defined for y faces
+//       with periodic x and z.
 //
 // Parity status: every function is pinned by the tests in tests/ (moment
 // identities, rest state, conservation, forcing, Taylor-Green and shear-wave
@@ -69,7 +76,7 @@ const double CS2 = 1.0 / 3.0;
 const double CS4 = CS2 * CS2;
 const double CS6 = CS4 * CS2;
 
-enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1, BC_FREESLIP = 2, BC_INFLOW = 3, BC_OUTFLOW = 4 };
+enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1, BC_FREESLIP = 2, BC_INFLOW = 3, BC_OUTFLOW = 4, BC_NEE_WALL = 5 };
 
 struct Lattice {
     int c[27][3];
@@ -292,6 +299,17 @@ void source_post(const Sim<T>& s, int64_t x, int64_t y, int64_t z, T out[27]) {
         for (int i = 0; i < 27; ++i) out[i] = eq[i] + (1.0 - w) * neq[i];
         return;
     }
+    const bool nee_lo = s.bc[2] == BC_NEE_WALL && y == 0, nee_hi = s.bc[3] == BC_NEE_WALL && y == s.n[1] - 1;
+    if (nee_lo || nee_hi) {  // R10
+        node_moments(s, s.idx(x, nee_lo ? 1 : s.n[1] - 2, z), rho, u, pi);
+        const T uB[3] = {0.0, 0.0, 0.0};
+        T eq[27], neq[27];
+        feq3(rho, uB, eq);
+        fneq3(pi, u, neq);
+        const double w = s.omega_at(z);
+        for (int i = 0; i < 27; ++i) out[i] = eq[i] + (1.0 - w) * neq[i];
+        return;
+    }
     int64_t zs = z;
     if (s.bc[5] == BC_OUTFLOW && z == s.n[2] - 1) zs = s.n[2] - 2;  // zero-gradient copy
     int64_t node = s.idx(x, y, zs);
@@ -309,10 +327,12 @@ void step_once(Sim<T>& s) {
     std::fill(s.fnew.begin(), s.fnew.end(), nan);
     const int64_t zlo = (s.bc[4] == BC_INFLOW) ? 0 : s.lo(2);
     const int64_t zhi = (s.bc[5] == BC_OUTFLOW) ? nz - 1 : s.hi(2);
+    const int64_t ylo = (s.bc[2] == BC_NEE_WALL) ? 0 : s.lo(1);
+    const int64_t yhi = (s.bc[3] == BC_NEE_WALL) ? s.n[1] - 1 : s.hi(1);
 #pragma omp parallel for schedule(static)
     for (int64_t z = zlo; z <= zhi; ++z) {
         T post[27];
-        for (int64_t y = s.lo(1); y <= s.hi(1); ++y)
+        for (int64_t y = ylo; y <= yhi; ++y)
             for (int64_t x = s.lo(0); x <= s.hi(0); ++x) {
                 source_post(s, x, y, z, post);
                 const bool ghost = !s.interior(x, y, z);
@@ -379,8 +399,10 @@ int validate_and_init(Sim<T>* s, const int64_t dims[3], double tau, const double
     for (int f = 0; f < 6; ++f) {
         if (bc[f] == BC_INFLOW && f != 4) return -3;
         if (bc[f] == BC_OUTFLOW && f != 5) return -3;
-        if (bc[f] < BC_PERIODIC || bc[f] > BC_OUTFLOW) return -3;
+        if (bc[f] < BC_PERIODIC || bc[f] > BC_NEE_WALL) return -3;
+        if (bc[f] == BC_NEE_WALL && f != 2 && f != 3) return -3;
     }
+    if ((bc[2] == BC_NEE_WALL || bc[3] == BC_NEE_WALL) && (bc[0] != BC_PERIODIC || bc[4] != BC_PERIODIC)) return -3;
     if ((bc[4] == BC_INFLOW) != (bc[5] == BC_OUTFLOW)) return -3;
     s->omega = 1.0 / tau;
     for (int a = 0; a < 3; ++a) s->F[a] = F ? F[a] : 0.0;

@@ -287,6 +287,38 @@ def test_poiseuille_second_order():
     assert math.log2(e8 / e16) > 1.8 and math.log2(e16 / e32) > 1.8
 
 
+def _poiseuille_nee_error(H, tau=0.8, g=1e-6):
+    """Channel with thread-safe NEE no-slip walls on the nodes y = 0 and y = H."""
+    ny = H + 1
+    dims = (3, ny, 3)
+    N = 3 * ny * 3
+    nu = CS2 * (tau - 0.5)
+    y = np.tile(np.repeat(np.arange(ny, dtype=float), 3), 3)
+    exact = g / (2 * nu) * y * (H - y)
+    fluid = (y >= 1) & (y <= ny - 2)
+    u = np.zeros((3, N))
+    u[0] = np.where(fluid, exact, 0.0)
+    pi = np.zeros((6, N))
+    pi[3] = np.where(fluid, -CS2 * tau * g / (2 * nu) * (H - 2 * y), 0.0)
+    s = oracle.OracleSim(dims, tau, force=(g, 0, 0), bc=(0, 0, oracle.NEE_WALL, oracle.NEE_WALL, 0, 0))
+    s.init_moments(np.ones(N), u, pi)
+    s.step(int(3 * H * H / nu))
+    _, uu, _ = s.get_moments()
+    e = uu[0][fluid] - exact[fluid]
+    return np.sqrt(np.mean(e ** 2)) / np.sqrt(np.mean(exact[fluid] ** 2))
+
+
+@pytest.mark.slow
+def test_poiseuille_nee_walls_second_order():
+    """Thread-safe NEE no-slip walls (Sec. 2.3, Eq. neq_final with u_B = 0): the
+    steady channel between walls on the nodes y = 0, H approaches the parabola
+    g y (H - y) / (2 nu) at second order, as the extrapolation argument of
+    Sec. 2.3 states."""
+    e8, e16, e32 = (_poiseuille_nee_error(H) for H in (8, 16, 32))
+    assert e8 < 0.06
+    assert math.log2(e8 / e16) > 1.8 and math.log2(e16 / e32) > 1.8
+
+
 def test_freeslip_neumann_mode_decay():
     """u_x = A cos(pi (y - 1/2) / H) between free-slip walls at y = 1/2, H + 1/2 decays at nu (pi/H)^2."""
     H, tau, A = 32, 0.8, 0.01
