@@ -416,9 +416,21 @@ def main():
     adj = None
     if not args.no_adjoint and rank == 0:
         adj = time_adjoint(T, torch, stream)
-    jet = None
+    extra = None
     if not args.no_extra and rank == 0:
-        jet = time_jet_paper(T, torch, stream)
+        # the same channel with the paper's thread-safe NEE no-slip walls, and the paper's jet set-up
+        prm_nee = dict(prm)
+        prm_nee["bc"] = (0, 0, 5, 5, 0, 0)
+        k_nee = min(args.steps, 500)
+        msn, nn, dn, cn, _, _ = time_device(T, torch, prm_nee, state, args.precision, kernel, k_nee, args.warmup,
+                                            stream, None)
+        extra = {"channel_nee_walls": {
+                     "workload": "turbulent channel %dx%dx%d with thread-safe NEE no-slip walls on y=0,%d "
+                                 "(Eq. neq_final, u_B = 0); %s storage" % (args.nx, args.ny, args.nz, args.ny - 1,
+                                                                           args.precision),
+                     "value": job_mlups(nn, 1, k_nee, msn), "unit": "MLUPS", "steps": k_nee,
+                     "ms_per_step": msn / k_nee, "status": cn},
+                 "jet_paper": time_jet_paper(T, torch, stream)}
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(prm, args.cpu_seconds)
@@ -441,7 +453,7 @@ def main():
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "adjoint": adj,
-            "workloads": {"jet_paper": jet} if jet else None,
+            "workloads": extra,
             "clocks": ck,
             "diagnostics_after_timed": {"mass": diag["mass"], "max_speed": diag["max_speed"], "status": code},
         }

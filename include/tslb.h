@@ -61,7 +61,13 @@ typedef enum tslb_bc {
     TSLB_BC_BOUNCEBACK = 1, /* halfway bounce-back no-slip wall (y faces only) */
     TSLB_BC_FREESLIP = 2,   /* halfway specular-reflection wall (x or y faces) */
     TSLB_BC_INFLOW = 3,     /* z- only: thread-safe Hermite non-equilibrium inflow, Eq. neq_final */
-    TSLB_BC_OUTFLOW = 4     /* z+ only: zero-gradient outflow (moments of the adjacent layer) */
+    TSLB_BC_OUTFLOW = 4,    /* z+ only: zero-gradient outflow (moments of the adjacent layer) */
+    TSLB_BC_NEE_WALL = 5    /* y faces only, with periodic x and z: no-slip wall on the boundary layer by
+                               the thread-safe non-equilibrium extrapolation (Sec. 2.3, Eq. neq_final with
+                               imposed momentum u_B = 0): each boundary node emits
+                               f^eq(rho_F, 0) + (1 - omega) Hermite f^neq(Pi^neq, u of x_F), x_F the
+                               adjacent interior node; the wall is on the node, so the channel half-width
+                               is (ny - 1)/2 */
 } tslb_bc;
 
 typedef enum tslb_precision {

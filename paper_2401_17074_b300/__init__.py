@@ -22,7 +22,7 @@ TSLB_ERR_UNSTABLE = -5
 TSLB_ERR_STATE = -6
 
 TSLB_D3Q27 = 27
-PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
+PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL = 0, 1, 2, 3, 4, 5
 FP32, BF16, FP16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED = 0, 1, 2

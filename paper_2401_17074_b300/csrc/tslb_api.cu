@@ -158,7 +158,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     if (lattice != TSLB_D3Q27) return fail(nullptr, TSLB_ERR_UNSUPPORTED, "only TSLB_D3Q27 is implemented");
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, TSLB_ERR_INVALID, "tau must be > 1/2");
     for (int f = 0; f < 6; ++f)
-        if (bc[f] < TSLB_BC_PERIODIC || bc[f] > TSLB_BC_OUTFLOW)
+        if (bc[f] < TSLB_BC_PERIODIC || bc[f] > TSLB_BC_NEE_WALL)
             return fail(nullptr, TSLB_ERR_INVALID, "unknown boundary code");
     for (int a = 0; a < 3; ++a) {
         const bool p0 = bc[2 * a] == TSLB_BC_PERIODIC, p1 = bc[2 * a + 1] == TSLB_BC_PERIODIC;
@@ -172,12 +172,12 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "x and y faces must match pairwise");
     if (!(bx == TSLB_BC_PERIODIC || bx == TSLB_BC_FREESLIP))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "x faces: periodic or free-slip");
-    if (!(by == TSLB_BC_PERIODIC || by == TSLB_BC_FREESLIP || by == TSLB_BC_BOUNCEBACK))
-        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "y faces: periodic, bounce-back or free-slip");
+    if (!(by == TSLB_BC_PERIODIC || by == TSLB_BC_FREESLIP || by == TSLB_BC_BOUNCEBACK || by == TSLB_BC_NEE_WALL))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "y faces: periodic, bounce-back, free-slip or NEE wall");
     if (!((bz0 == TSLB_BC_PERIODIC && bz1 == TSLB_BC_PERIODIC) || (bz0 == TSLB_BC_INFLOW && bz1 == TSLB_BC_OUTFLOW)))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "z faces: periodic, or inflow (z-) with outflow (z+)");
-    if (by == TSLB_BC_BOUNCEBACK && (bx != TSLB_BC_PERIODIC || bz0 != TSLB_BC_PERIODIC))
-        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "bounce-back y walls need periodic x and z");
+    if ((by == TSLB_BC_BOUNCEBACK || by == TSLB_BC_NEE_WALL) && (bx != TSLB_BC_PERIODIC || bz0 != TSLB_BC_PERIODIC))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "bounce-back and NEE y walls need periodic x and z");
 
     tslb_options o;
     if (opt) o = *opt;
@@ -456,7 +456,7 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out) {
     out->momentum[1] = d[2];
     out->momentum[2] = d[3];
     out->kinetic_energy = d[4];
-    const bool ywalls = h->bc[2] == TSLB_BC_BOUNCEBACK;
+    const bool ywalls = h->bc[2] == TSLB_BC_BOUNCEBACK || h->bc[2] == TSLB_BC_NEE_WALL;
     out->wall_shear = ywalls ? d[5] / (2.0 * (double)h->g.nx * (double)h->g.nz) : 0.0;
     out->max_speed = d[6];
     out->nonfinite = (int64_t)d[7];

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) diag_partial_kernel(const typename Codec:
                                                            double* __restrict__ part) {
     double acc[NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
     const long long total = g.plane * g.nz;
-    const bool ywalls = g.bc[2] == TSLB_BC_BOUNCEBACK;
+    const bool ywalls = g.bc[2] == TSLB_BC_BOUNCEBACK || g.bc[2] == TSLB_BC_NEE_WALL;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < total;
          n += (long long)gridDim.x * blockDim.x) {
         float v[NFIELDS];

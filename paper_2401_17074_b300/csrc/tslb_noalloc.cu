@@ -105,8 +105,8 @@ extern "C" int tslb_diagnostics_noalloc(const double* rho, const double* u, cons
     long long ext[3];
     int lo[3];
     for (int a = 0; a < 3; ++a) {
-        if (bc[2 * a] < TSLB_BC_PERIODIC || bc[2 * a] > TSLB_BC_OUTFLOW || bc[2 * a + 1] < TSLB_BC_PERIODIC ||
-            bc[2 * a + 1] > TSLB_BC_OUTFLOW)
+        if (bc[2 * a] < TSLB_BC_PERIODIC || bc[2 * a] > TSLB_BC_NEE_WALL || bc[2 * a + 1] < TSLB_BC_PERIODIC ||
+            bc[2 * a + 1] > TSLB_BC_NEE_WALL)
             return na_fail(TSLB_ERR_INVALID, "unknown boundary code");
         const bool per = bc[2 * a] == TSLB_BC_PERIODIC;
         if (per != (bc[2 * a + 1] == TSLB_BC_PERIODIC))
@@ -138,7 +138,7 @@ extern "C" int tslb_diagnostics_noalloc(const double* rho, const double* u, cons
         partials = g_partials_addr[dev];
     }
     const int nblocks = (int)((total + NA_NODES_PER_BLOCK - 1) / NA_NODES_PER_BLOCK);
-    const bool ywalls = bc[2] == TSLB_BC_BOUNCEBACK;
+    const bool ywalls = bc[2] == TSLB_BC_BOUNCEBACK || bc[2] == TSLB_BC_NEE_WALL;
     const double shear_scale = 1.0 - 0.5 / tau;
     const double shear_norm = ywalls ? 1.0 / (2.0 * (double)ext[0] * (double)ext[2]) : 0.0;
     const long long fN = (long long)dims[0] * dims[1] * dims[2];

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
                 int s[3] = {own[0] - cx, own[1] - cy, own[2] - cz};
                 int c[3] = {cx, cy, cz};
                 bool bounce = false;
-                int ghost = 0;  // 1 inflow layer, 2 outflow layer
+                int ghost = 0;  // 1 inflow layer, 2 outflow layer, 3 NEE wall layer
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     if (s[a] >= 0 && s[a] < ext[a]) continue;
@@ -67,6 +67,9 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
                     } else if (face == TSLB_BC_FREESLIP) {
                         s[a] = own[a];
                         c[a] = -c[a];
+                    } else if (face == TSLB_BC_NEE_WALL) {
+                        ghost = 3;
+                        s[a] = s[a] < 0 ? 0 : ext[a] - 1;  // x_F: the adjacent interior node
                     } else if (face == TSLB_BC_INFLOW) {
                         ghost = 1;
                         s[a] = 0;
@@ -78,6 +81,15 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
                 float gi;
                 if (bounce) {
                     gi = pop_dev216(Aown, -cx, -cy, -cz);
+                } else if (ghost == 3) {
+                    // the wall node emits f^eq(rho_F, 0) + (1 - omega) f^neq(Pi_F, u_F) (Eq. neq_final)
+                    const long long fidx = (long long)s[0] + (long long)g.nx * s[1] + g.plane * s[2];
+                    float m[NFIELDS];
+                    load_node<Codec>(src, g, p, fidx, m);
+                    float A[NMODES];
+                    post_modes(m[F_DRHO], 0.f, 0.f, 0.f, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
+                               omega1_at(p, s[2] + g.lo[2]), A);
+                    gi = pop_dev216(A, c[0], c[1], c[2]);
                 } else if (ghost == 1) {
                     const long long fidx = (long long)s[0] + (long long)g.nx * s[1];  // x_F: first interior layer
                     float m[NFIELDS];

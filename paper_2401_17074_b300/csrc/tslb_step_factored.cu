@@ -306,11 +306,11 @@ struct Ctx {
     int tid, lane, warp, x, y, xl, yl;
     unsigned col, plane;
     int z0, z1, np;  // march covers planes z0-1 .. z1 (np of them)
-    bool zper, ybb, store, out_row, row_lo, row_hi, zero_row, xlo_mirror, xhi_mirror;
+    bool zper, ybb, store, out_row, row_lo, row_hi, zero_row, nee_row, xlo_mirror, xhi_mirror;
     int offLv, offRv, offLs, offRs;  // y-exchange read offsets (float4 / float units, relative to a slot base)
 };
 
-template <class Codec, bool XFREE, bool SPONGE>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY>
 struct Kernel {
     typedef typename Codec::T T;
 
@@ -372,6 +372,12 @@ struct Kernel {
             if (!STEADY && inflow_ghost) {
                 const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
                 h = to_pairs(hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
+                                     om_pi));
+            } else if (NEEY && uni(c.nee_row)) {
+                // ghost row beyond an NEE wall: the wall node (whose column is
+                // clamped onto the adjacent fluid node) emits f^eq(rho_F, 0) +
+                // (1 - omega) f^neq(Pi_F, u_F), Eq. neq_final with u_B = 0
+                h = to_pairs(hermite(m[F_DRHO], 0.f, 0.f, 0.f, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
                                      om_pi));
             } else {
                 float F0, F1, F2;
@@ -570,11 +576,11 @@ struct Kernel {
     }
 };
 
-template <class Codec, bool XFREE, bool SPONGE>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY>
 __global__ void __launch_bounds__(NT, 1)
     step_factored_kernel(const typename Codec::T* __restrict__ src, typename Codec::T* __restrict__ dst, Geometry g,
                          Physics p, int zchunk) {
-    typedef Kernel<Codec, XFREE, SPONGE> K;
+    typedef Kernel<Codec, XFREE, SPONGE, NEEY> K;
     extern __shared__ __align__(16) float ysm[];  // [2][YBUF] y exchange, then [2][PF::BUF] plane prefetch
     char* pfb = reinterpret_cast<char*>(ysm) + 2 * YBUF;
     float* corr = reinterpret_cast<float*>(pfb + 2 * K::PF::BUF);
@@ -609,6 +615,7 @@ __global__ void __launch_bounds__(NT, 1)
     c.row_lo = c.y == 0;
     c.row_hi = c.y == g.ny - 1;
     c.zero_row = c.ybb && (c.y == -1 || c.y == g.ny);
+    c.nee_row = NEEY && (c.y == -1 || c.y == g.ny);
     // y-exchange read offsets: the row below / above, or -- on a free-slip wall
     // row -- the node's own value of the opposite population (p- slots sit
     // 2 float4 slots after the p+ slots, the scalar p- one float slot after p+)
@@ -642,9 +649,9 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
-template <class Codec, bool XFREE, bool SPONGE>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY>
 cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    auto kern = step_factored_kernel<Codec, XFREE, SPONGE>;
+    auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY>;
     static bool configured[64] = {};
     const int dev = h->device;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -683,8 +690,12 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
 template <class Codec>
 cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Physics& p) {
     const bool xfree = h->g.bc[0] == TSLB_BC_FREESLIP, sponge = p.omega1_z != nullptr;
-    if (xfree) return sponge ? launch_t<Codec, true, true>(h, src, dst, p) : launch_t<Codec, true, false>(h, src, dst, p);
-    return sponge ? launch_t<Codec, false, true>(h, src, dst, p) : launch_t<Codec, false, false>(h, src, dst, p);
+    // NEE y walls come with periodic x (checked at create)
+    if (h->g.bc[2] == TSLB_BC_NEE_WALL)
+        return sponge ? launch_t<Codec, false, true, true>(h, src, dst, p) : launch_t<Codec, false, false, true>(h, src, dst, p);
+    if (xfree)
+        return sponge ? launch_t<Codec, true, true, false>(h, src, dst, p) : launch_t<Codec, true, false, false>(h, src, dst, p);
+    return sponge ? launch_t<Codec, false, true, false>(h, src, dst, p) : launch_t<Codec, false, false, false>(h, src, dst, p);
 }
 
 }  // namespace

@@ -19,7 +19,7 @@ import math
 import numpy as np
 
 CS2 = 1.0 / 3.0
-PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
+PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL = 0, 1, 2, 3, 4, 5
 
 
 def _coords(dims):

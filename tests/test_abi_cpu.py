@@ -70,6 +70,10 @@ def _create_code(dims=(8, 8, 8), tau=0.6, bc=(0,) * 6, lattice=T.TSLB_D3Q27, opt
     (dict(bc=(0, 0, 0, 0, 4, 3)), T.TSLB_ERR_UNSUPPORTED),
     (dict(bc=(0, 0, 1, 1, 3, 4)), T.TSLB_ERR_UNSUPPORTED),
     (dict(bc=(0, 0, 9, 9, 0, 0)), T.TSLB_ERR_INVALID),
+    (dict(bc=(5, 5, 0, 0, 0, 0)), T.TSLB_ERR_UNSUPPORTED),
+    (dict(bc=(2, 2, 5, 5, 0, 0)), T.TSLB_ERR_UNSUPPORTED),
+    (dict(bc=(0, 0, 5, 5, 3, 4)), T.TSLB_ERR_UNSUPPORTED),
+    (dict(bc=(0, 0, 0, 0, 5, 5)), T.TSLB_ERR_UNSUPPORTED),
 ])
 def test_create_rejects_bad_arguments(kw, code):
     c, h = _create_code(**kw)

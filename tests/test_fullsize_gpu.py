@@ -160,6 +160,18 @@ def test_channel_full_size_sampled(cuda_ok):
 
 
 @pytest.mark.gpu
+def test_channel_nee_walls_full_size_sampled(cuda_ok):
+    """The bench channel with thread-safe NEE no-slip walls instead of bounce-back."""
+    prm = dict(W.channel_params())  # 512 x 130 x 256
+    prm["bc"] = (0, 0, 5, 5, 0, 0)
+    state = W.channel_state(prm, seed=1)
+    gpu = _run_gpu(prm, state)
+    cols = [{0: 0, 2: 0}, {0: 511, 2: 255}, {0: 255, 2: 128}, {0: 30, 2: 17}, {0: 29, 2: 200}]
+    pairs = [_compare_column(gpu, state, prm["dims"], prm["tau"], prm["force"], prm["bc"], c) for c in cols]
+    _check(pairs, 3e-6, tol_pi=2e-5)
+
+
+@pytest.mark.gpu
 def test_jet_full_size_sampled(cuda_ok):
     prm = W.jet_params()  # 256 x 256 x 640, inflow z = 0, outflow z = 639, free-slip sides
     dims = prm["dims"]

@@ -139,6 +139,29 @@ def test_bounceback_wall_rows(cuda_ok, kernel, dims):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("dims", [(6, 4, 5), (33, 18, 6), (40, 38, 7)], ids=["two-rows", "one-tile", "ragged-tiles"])
+def test_nee_wall_rows(cuda_ok, kernel, dims):
+    """Thread-safe NEE no-slip walls (Sec. 2.3, Eq. neq_final with u_B = 0) on
+    the y boundary layers: random state and body force, same tile cases as the
+    bounce-back test."""
+    bc = (0, 0, 5, 5, 0, 0)
+    state = W.random_state(dims, seed=30)
+    errs, _, _ = run_pair(dims, 0.6, state, 3, kernel, bc=bc, force=(2e-5, -1e-5, 1e-5))
+    assert_all_below(errs, 3e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_nee_wall_channel_small(cuda_ok, kernel):
+    """Forced channel between NEE walls at the bench relaxation time, 30 steps."""
+    prm = W.channel_params(nx=40, ny=34, nz=20)
+    state = W.channel_state(prm, seed=2)
+    bc = (0, 0, 5, 5, 0, 0)
+    errs, _, _ = run_pair(prm["dims"], prm["tau"], state, 30, kernel, bc=bc, force=prm["force"])
+    assert errs["ux"] <= 1e-5, errs
+    assert_all_below(errs, 1e-4)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_freeslip_random_state(cuda_ok, kernel):
     dims = (7, 6, 5)
     bc = (2, 2, 2, 2, 0, 0)
