@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tslb_oracle.cpp")
+_SRC2 = os.path.join(_HERE, "tslb_oracle2d.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL = 0, 1, 2, 3, 4, 5
@@ -27,9 +28,10 @@ _lib = None
 
 def build(force=False):
     """Compile the oracle shared library with g++ -O3 -fopenmp."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(p) for p in (_SRC, _SRC2))
+    if force or stale:
         subprocess.check_call(["g++", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c++17",
-                               "-o", _LIB, _SRC])
+                               "-o", _LIB, _SRC, _SRC2])
     return _LIB
 
 
@@ -63,6 +65,16 @@ def lib():
         L.orc_get_populations.argtypes = [ctypes.c_void_p, dp]
         L.orc_time.argtypes = [ctypes.c_void_p]
         L.orc_time.restype = ctypes.c_int64
+        L.orc2_lattice.argtypes = [ip, dp]
+        L.orc2_feq3.argtypes = [ctypes.c_double, dp, dp]
+        L.orc2_fneq3.argtypes = [dp, dp, dp]
+        L.orc2_moments.argtypes = [dp, dp, dp, dp]
+        L.orc2_create.argtypes = [i64p, ctypes.c_double, dp, ip, ip]
+        L.orc2_create.restype = ctypes.c_void_p
+        L.orc2_destroy.argtypes = [ctypes.c_void_p]
+        L.orc2_init_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
+        L.orc2_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        L.orc2_get_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
         L.orc_complex_run.argtypes = [i64p, ctypes.c_double, ip, dp, dp, dp, dp, dp, ctypes.c_int64, dp, dp]
         _lib = L
     return _lib
@@ -233,3 +245,78 @@ def complex_step_energy(dims, tau, bc, rho, u, pi, F_re, F_im, nsteps):
     if st != 0:
         raise ValueError("oracle rejected the configuration (status %d)" % st)
     return complex(jr.value, ji.value)
+
+
+# ---- D2Q9 ------------------------------------------------------------------------
+
+def lattice2d():
+    """Return (c [9,2] int, w [9]) of the D2Q9 oracle."""
+    c = np.zeros((9, 2), dtype=np.int32)
+    w = np.zeros(9)
+    lib().orc2_lattice(c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(w))
+    return c, w
+
+
+def feq3_2d(rho, u):
+    out = np.zeros(9)
+    lib().orc2_feq3(float(rho), _d(_f64(u)), _d(out))
+    return out
+
+
+def fneq3_2d(pi3, u):
+    """pi3 = (xx, yy, xy)."""
+    out = np.zeros(9)
+    lib().orc2_fneq3(_d(_f64(pi3)), _d(_f64(u)), _d(out))
+    return out
+
+
+def moments2d(f):
+    rho = np.zeros(1)
+    u = np.zeros(2)
+    pi3 = np.zeros(3)
+    lib().orc2_moments(_d(_f64(f)), _d(rho), _d(u), _d(pi3))
+    return rho[0], u, pi3
+
+
+class OracleSim2D:
+    """Population-based FP64 D2Q9 TSLB simulation on a full nx*ny lattice.
+
+    bc = (x-, x+, y-, y+): PERIODIC, or BOUNCEBACK on the y faces (solid
+    layers y = 0 and y = ny-1).  Moments: rho[N], u[2][N], pi[3][N] (xx, yy, xy).
+    """
+
+    def __init__(self, dims, tau, force=(0.0, 0.0), bc=(0, 0, 0, 0)):
+        self.dims = (int(dims[0]), int(dims[1]))
+        self.N = self.dims[0] * self.dims[1]
+        d = np.array(self.dims, dtype=np.int64)
+        b = np.array(bc, dtype=np.int32)
+        st = ctypes.c_int(0)
+        self._h = lib().orc2_create(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(tau), _d(_f64(force)),
+                                    b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(st))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration (status %d)" % st.value)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc2_destroy(self._h)
+            self._h = None
+
+    def init_moments(self, rho, u, pi=None):
+        rho = _f64(rho).reshape(-1)
+        u = _f64(u).reshape(-1)
+        keep = _f64(pi).reshape(-1) if pi is not None else None
+        pi_p = _d(keep) if keep is not None else None
+        assert rho.size == self.N and u.size == 2 * self.N
+        lib().orc2_init_moments(self._h, _d(rho), _d(u), pi_p)
+
+    def step(self, n=1):
+        st = lib().orc2_step(self._h, int(n))
+        if st != 0:
+            raise RuntimeError("oracle step failed (%d)" % st)
+
+    def get_moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros(2 * self.N)
+        pi = np.zeros(3 * self.N)
+        lib().orc2_get_moments(self._h, _d(rho), _d(u), _d(pi))
+        return rho, u.reshape(2, self.N), pi.reshape(3, self.N)
