@@ -303,6 +303,36 @@ def time_jet_paper(T, torch, stream, steps=200, warmup=20):
             "ms_per_step": ms / steps, "interior_nodes": nodes, "max_speed": d["max_speed"], "status": code}
 
 
+def time_channel2d(T, torch, stream, hbm, steps=500, warmup=20):
+    """The D2Q9 variant on its channel (8192 x 2050, bounce-back walls, 16.78 M
+    interior nodes); FP32 storage, 48 algorithmic bytes per node."""
+    from paper_2401_17074_b300 import workloads as W
+    prm = W.channel2d_params()
+    state = W.channel2d_state(prm, seed=1)
+    s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], lattice=T.TSLB_D2Q9,
+                 stream=stream.cuda_stream)
+    s.init_moments(*state)
+    s.step(warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    d, code = s.diagnostics()
+    nodes = s.interior_nodes()
+    s.close()
+    achieved = 48.0 * nodes / (ms * 1e-3 / steps) / 1e9
+    return {"workload": "D2Q9 channel %dx%d, bounce-back walls y=0,%d, tau=%.3f; fp32 storage"
+                        % (prm["dims"][0], prm["dims"][1], prm["dims"][1] - 1, prm["tau"]),
+            "value": job_mlups(nodes, 1, steps, ms), "unit": "MLUPS", "steps": steps, "ms_per_step": ms / steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "algorithmic_bytes_per_node": 48, "kernel": "tslb_step2d"},
+            "status": code}
+
+
 def time_adjoint(T, torch, stream, n=128, nsteps=64, k=16, tau=0.52):
     """Forward (with checkpoints) and discrete adjoint of the force gradient on an n^3 periodic box."""
     from paper_2401_17074_b300 import workloads as W
@@ -430,7 +460,8 @@ def main():
                                                                            args.precision),
                      "value": job_mlups(nn, 1, k_nee, msn), "unit": "MLUPS", "steps": k_nee,
                      "ms_per_step": msn / k_nee, "status": cn},
-                 "jet_paper": time_jet_paper(T, torch, stream)}
+                 "jet_paper": time_jet_paper(T, torch, stream),
+                 "d2q9_channel": time_channel2d(T, torch, stream, hbm)}
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(prm, args.cpu_seconds)

@@ -53,7 +53,13 @@ typedef enum tslb_status {
     TSLB_ERR_STATE = -6        /* call not valid in the handle's current state */
 } tslb_status;
 
-enum { TSLB_D3Q27 = 27 };
+/* Lattices.  TSLB_D2Q9 is the two-dimensional variant of the same step (the
+ * recursion of Eq. noneqts on D1Q3 x D1Q3): dims = (nx, ny, 1) with periodic z
+ * faces, periodic x, periodic or TSLB_BC_BOUNCEBACK y faces, FP32 storage, the
+ * constant body force only (no force field, adjoint, inflow or sponge; the
+ * `kernel` option is ignored).  Its moment arrays keep the three-dimensional
+ * layouts: u_z, Pi_zz, Pi_xz and Pi_yz are ignored on input and returned as 0. */
+enum { TSLB_D3Q27 = 27, TSLB_D2Q9 = 9 };
 
 /* Face boundary conditions, indexed bc[0..5] = x-, x+, y-, y+, z-, z+. */
 typedef enum tslb_bc {

@@ -22,6 +22,7 @@ TSLB_ERR_UNSTABLE = -5
 TSLB_ERR_STATE = -6
 
 TSLB_D3Q27 = 27
+TSLB_D2Q9 = 9
 PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL = 0, 1, 2, 3, 4, 5
 FP32, BF16, FP16 = 0, 1, 2
 HOST, DEVICE = 0, 1
@@ -231,7 +232,8 @@ class Solver:
     """Owns one TSLB handle.  Arrays follow the C ABI layouts (full lattice, x fastest)."""
 
     def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05, pi_ref=1e-3,
-                 kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None, sponge=None):
+                 kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None, sponge=None,
+                 lattice=None):
         """inflow: dict(center2, diameter, u_jet, noise_amp, seed[, noise="uniform" | "gaussian"]);
         sponge: (width, K) viscosity layer towards the z+ face (tslb_options.sponge_width / sponge_k)."""
         o = tslb_options_default()
@@ -257,7 +259,7 @@ class Solver:
             o.sponge_k = float(sponge[1])
         self.dims = tuple(int(d) for d in dims)
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
-        self._h = tslb_create(self.dims, tau, force, bc, o)
+        self._h = tslb_create(self.dims, tau, force, bc, o, lattice=TSLB_D3Q27 if lattice is None else lattice)
 
     @property
     def handle(self):

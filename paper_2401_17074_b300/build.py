@@ -15,6 +15,7 @@ SOURCES = [
     "tslb_step_factored.cu",
     "tslb_adjoint.cu",
     "tslb_noalloc.cu",
+    "tslb_step2d.cu",
 ]
 
 NVCC_FLAGS = [

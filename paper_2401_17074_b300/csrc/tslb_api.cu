@@ -119,6 +119,7 @@ Physics make_physics(const tslb_s* h) {
 bool use_factored(const tslb_s* h) { return h->kernel != TSLB_KERNEL_DIRECT && factored_supports(h); }
 
 cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p) {
+    if (h->lattice == TSLB_D2Q9) return launch_step2d(h, src, dst, p);
     return use_factored(h) ? launch_step_factored(h, src, dst, p) : launch_step_direct(h, src, dst, p);
 }
 
@@ -126,7 +127,7 @@ cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const P
 
 namespace {
 
-size_t state_bytes(const tslb_s* h) { return (size_t)tslb::NFIELDS * h->g.fstride * h->elem; }
+size_t state_bytes(const tslb_s* h) { return (size_t)h->nfields * h->g.fstride * h->elem; }
 
 void drop_checkpoints(tslb_s* h) {
     if (!h->ckpts.empty()) cudaStreamSynchronize(h->stream);
@@ -155,7 +156,9 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
                 const int bc[6], const tslb_options* opt) {
     g_create_error.clear();
     if (!out || !dims || !bc) return fail(nullptr, TSLB_ERR_INVALID, "null argument");
-    if (lattice != TSLB_D3Q27) return fail(nullptr, TSLB_ERR_UNSUPPORTED, "only TSLB_D3Q27 is implemented");
+    if (lattice != TSLB_D3Q27 && lattice != TSLB_D2Q9)
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "lattices: TSLB_D3Q27 or TSLB_D2Q9");
+    const bool d2 = lattice == TSLB_D2Q9;
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, TSLB_ERR_INVALID, "tau must be > 1/2");
     for (int f = 0; f < 6; ++f)
         if (bc[f] < TSLB_BC_PERIODIC || bc[f] > TSLB_BC_NEE_WALL)
@@ -163,6 +166,10 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     for (int a = 0; a < 3; ++a) {
         const bool p0 = bc[2 * a] == TSLB_BC_PERIODIC, p1 = bc[2 * a + 1] == TSLB_BC_PERIODIC;
         if (p0 != p1) return fail(nullptr, TSLB_ERR_INVALID, "an axis mixes periodic and non-periodic faces");
+        if (d2 && a == 2) {
+            if (dims[2] != 1 || !p0) return fail(nullptr, TSLB_ERR_INVALID, "D2Q9 needs nz = 1 with periodic z faces");
+            continue;
+        }
         if (dims[a] < (p0 ? 3 : 4)) return fail(nullptr, TSLB_ERR_INVALID, "axis too short");
         if (dims[a] > (int64_t)1 << 30) return fail(nullptr, TSLB_ERR_INVALID, "axis too long");
     }
@@ -190,6 +197,10 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_INVALID, "unknown kernel choice");
     if (o.checkpoint_every < 0) return fail(nullptr, TSLB_ERR_INVALID, "checkpoint_every < 0");
     if (bz0 == TSLB_BC_INFLOW && o.inflow.diameter < 0) return fail(nullptr, TSLB_ERR_INVALID, "bad inflow diameter");
+    if (d2 && (bx != TSLB_BC_PERIODIC || !(by == TSLB_BC_PERIODIC || by == TSLB_BC_BOUNCEBACK)))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "D2Q9: periodic x, periodic or bounce-back y");
+    if (d2 && (o.precision != TSLB_FP32 || o.checkpoint_every != 0 || o.sponge_width != 0))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "D2Q9: FP32 storage, no checkpoints, no sponge layer");
     if (o.inflow.noise_kind != TSLB_NOISE_UNIFORM && o.inflow.noise_kind != TSLB_NOISE_GAUSSIAN)
         return fail(nullptr, TSLB_ERR_INVALID, "unknown inflow noise kind");
     if (o.sponge_width < 0 || o.sponge_width >= dims[2] || !(o.sponge_k >= 0.0) || !std::isfinite(o.sponge_k))
@@ -202,6 +213,8 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
 
     tslb_s* h = new tslb_s();
     h->device = o.device;
+    h->lattice = lattice;
+    h->nfields = d2 ? 6 : (int)tslb::NFIELDS;
     for (int a = 0; a < 3; ++a) h->dims[a] = dims[a];
     for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
     h->tau = tau;
@@ -250,7 +263,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         }
         h->own_stream = true;
     }
-    const size_t bytes = (size_t)tslb::NFIELDS * g.fstride * h->elem;
+    const size_t bytes = (size_t)h->nfields * g.fstride * h->elem;
     for (int b = 0; b < 2; ++b) {
         e = dev_alloc(&h->buf[b], bytes);
         if (e != cudaSuccess) {
@@ -346,6 +359,7 @@ int tslb_init_moments(tslb_t* h, const double* rho, const double* u, const doubl
 int tslb_set_force_field(tslb_t* h, const float* F, int where) {
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    if (h->lattice == TSLB_D2Q9) return fail(h, TSLB_ERR_UNSUPPORTED, "D2Q9 takes the constant body force only");
     cudaSetDevice(h->device);
     if (!F) {
         if (h->force_field) {
@@ -386,7 +400,7 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (nsteps < 0) return fail(h, TSLB_ERR_INVALID, "nsteps < 0");
     cudaSetDevice(h->device);
-    if (h->kernel == TSLB_KERNEL_FACTORED && !tslb::factored_supports(h))
+    if (h->lattice == TSLB_D3Q27 && h->kernel == TSLB_KERNEL_FACTORED && !tslb::factored_supports(h))
         return fail(h, TSLB_ERR_UNSUPPORTED, "the factored kernel does not support this configuration");
     const int k = h->checkpoint_every;
     for (int64_t s = 0; s < nsteps; ++s) {
@@ -471,6 +485,7 @@ int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int wher
     if (!dJdF) return fail(h, TSLB_ERR_INVALID, "null output");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
     if (h->omega1_z) return fail(h, TSLB_ERR_UNSUPPORTED, "the adjoint does not support a sponge layer");
+    if (h->lattice == TSLB_D2Q9) return fail(h, TSLB_ERR_UNSUPPORTED, "the adjoint is implemented for D3Q27");
     cudaSetDevice(h->device);
     std::string msg;
     const int r = tslb::adjoint_force_gradient(h, nsteps, dJdF, where, &msg);

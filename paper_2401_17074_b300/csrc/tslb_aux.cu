@@ -112,6 +112,7 @@ __global__ void diag_final_kernel(const double* __restrict__ part, int nblocks, 
 
 cudaError_t launch_encode(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst,
                           const Physics& p) {
+    if (h->lattice == TSLB_D2Q9) return launch_encode2d(h, rho, u, pi, dst);
     const long long total = h->g.plane * h->g.nz;
     const int threads = 256;
     const unsigned blocks = (unsigned)((total + threads - 1) / threads);
@@ -134,6 +135,7 @@ cudaError_t launch_encode(const tslb_s* h, const double* rho, const double* u, c
 }
 
 cudaError_t launch_decode(const tslb_s* h, const void* src, double* rho, double* u, double* pi, const Physics& p) {
+    if (h->lattice == TSLB_D2Q9) return launch_decode2d(h, src, rho, u, pi);
     const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
     const int threads = 256;
     const unsigned blocks = (unsigned)((fN + threads - 1) / threads);
@@ -155,6 +157,7 @@ cudaError_t launch_decode(const tslb_s* h, const void* src, double* rho, double*
 }
 
 cudaError_t launch_diag(const tslb_s* h, const void* src, const Physics& p, double* out_dev) {
+    if (h->lattice == TSLB_D2Q9) return launch_diag2d(h, src, out_dev);
     const int threads = 256;
     const double shear_scale = 1.0 - 0.5 * h->omega;
     switch (h->precision) {

@@ -398,9 +398,13 @@ __device__ __forceinline__ float inflow_uz(const Physics& p, long long x, long l
 
 }  // namespace tslb
 
+constexpr int NFIELDS_3D = 10;
+
 // ---- handle -----------------------------------------------------------------
 struct tslb_s {
     int device = 0;
+    int lattice = TSLB_D3Q27;
+    int nfields = NFIELDS_3D;  // stored moment fields per node (10, or 6 for D2Q9)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int64_t dims[3] = {0, 0, 0};
@@ -436,6 +440,11 @@ namespace tslb {
 
 // Launchers implemented in the kernel translation units.
 cudaError_t launch_step_direct(const tslb_s* h, const void* src, void* dst, const Physics& p);
+// D2Q9 variant (tslb_step2d.cu)
+cudaError_t launch_step2d(const tslb_s* h, const void* src, void* dst, const Physics& p);
+cudaError_t launch_encode2d(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst);
+cudaError_t launch_decode2d(const tslb_s* h, const void* src, double* rho, double* u, double* pi);
+cudaError_t launch_diag2d(const tslb_s* h, const void* src, double* out_dev);
 cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p);
 // The step kernel tslb_step uses for this handle (same choice, bitwise-identical results).
 cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p);

@@ -177,6 +177,39 @@ def jet_paper_params(nx=440, ny=440, nz=600, D=20, u_jet=0.05, re=7000.0, noise_
                 sponge=(sponge_width, sponge_k))
 
 
+# ---- D2Q9 channel (two-dimensional variant, 8192 x 2050) -----------------------
+
+def channel2d_params(nx=8192, ny=2050, u_tau=0.0035, tau=0.503):
+    """Bounce-back walls at y = 0 and y = ny-1 (solid layers), periodic x,
+    H = (ny-2)/2, body force g = u_tau^2 / H along x.  16.78 M interior nodes at
+    the default size (the same count as the three-dimensional channel)."""
+    H = (ny - 2) / 2.0
+    g = u_tau * u_tau / H
+    return dict(dims=(nx, ny, 1), tau=tau, force=(g, 0.0, 0.0), bc=(PERIODIC, PERIODIC, BOUNCEBACK, BOUNCEBACK,
+                                                                   PERIODIC, PERIODIC), H=H, u_tau=u_tau)
+
+
+def channel2d_state(prm, seed=1, noise=0.02, re_tau=180.0):
+    """Parabola to the log-law centreline speed plus uniform noise (as the 3-D
+    channel), Pi from the parabola's shear; arrays in the three-dimensional
+    layouts (u_z, Pi_zz, Pi_xz, Pi_yz zero)."""
+    nx, ny, _ = prm["dims"]
+    H, tau = prm["H"], prm["tau"]
+    Uc = prm["u_tau"] * (math.log(re_tau) / 0.41 + 5.0)
+    rng = np.random.default_rng(seed)
+    N = nx * ny
+    y = np.repeat(np.arange(ny, dtype=float), nx)
+    eta = (y - 0.5) / (2.0 * H)  # walls halfway between the solid and first fluid layers
+    ux = np.clip(4.0 * Uc * eta * (1.0 - eta), 0.0, None)
+    u = np.zeros((3, N))
+    u[0] = ux + noise * Uc * rng.uniform(-1.0, 1.0, N)
+    u[1] = noise * Uc * rng.uniform(-1.0, 1.0, N)
+    dudy = 4.0 * Uc * (1.0 - 2.0 * eta) / (2.0 * H)
+    pi = np.zeros((6, N))
+    pi[3] = -CS2 * tau * dudy
+    return np.ones(N), u, pi
+
+
 # ---- adjoint box (128^3 periodic, divergence-free random velocity) ----------
 
 def divfree_random(n=128, u_rms=0.02, kmax=8, tau=0.52, seed=5):

@@ -108,6 +108,21 @@ def test_bad_sponge_and_noise_rejected():
     assert c == T.TSLB_ERR_INVALID
 
 
+def test_d2q9_create_rules():
+    # nz must be 1 with periodic z faces; x periodic; y periodic or bounce-back
+    for dims, bc, code in (((8, 8, 2), (0,) * 6, T.TSLB_ERR_INVALID),
+                           ((8, 8, 1), (0, 0, 0, 0, 3, 4), T.TSLB_ERR_INVALID),
+                           ((8, 8, 1), (2, 2, 0, 0, 0, 0), T.TSLB_ERR_UNSUPPORTED),
+                           ((8, 8, 1), (0, 0, 2, 2, 0, 0), T.TSLB_ERR_UNSUPPORTED)):
+        c, h = _create_code(dims=dims, bc=bc, lattice=T.TSLB_D2Q9)
+        assert c == code, (dims, bc, c)
+        assert not h.value
+    o = T.tslb_options_default()
+    o.precision = T.BF16
+    c, h = _create_code(dims=(8, 8, 1), lattice=T.TSLB_D2Q9, opt=o)
+    assert c == T.TSLB_ERR_UNSUPPORTED
+
+
 def test_null_handle_calls_fail_cleanly():
     L = T.load()
     assert L.tslb_step(None, 1) == T.TSLB_ERR_INVALID
