@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the paper-jet workload line")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workload lines")
+    ap.add_argument("--only", default=None, choices=["d2q9"], help="time one extra workload alone (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -407,6 +408,12 @@ def main():
         torch.cuda.set_device(0)
     import paper_2401_17074_b300 as T
     T.load()
+    if args.only == "d2q9":
+        hbm, hbm_src = measured_peaks()
+        line = time_channel2d(T, torch, torch.cuda.Stream(), hbm, steps=args.steps, warmup=args.warmup)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     kernel = {"auto": T.KERNEL_AUTO, "direct": T.KERNEL_DIRECT, "factored": T.KERNEL_FACTORED}[args.kernel]
     prm, state = make_state(args.nx, args.ny, args.nz)
     stream = torch.cuda.Stream()
