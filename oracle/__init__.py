@@ -55,6 +55,7 @@ def lib():
         L.orc_inflow_noise_gauss.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
         L.orc_inflow_noise_gauss.restype = ctypes.c_double
         L.orc_set_sponge.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]
+        L.orc_set_forcing.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_create.argtypes = [i64p, ctypes.c_double, dp, ip, i64p, dp, ctypes.c_uint64, ip]
         L.orc_create.restype = ctypes.c_void_p
         L.orc_destroy.argtypes = [ctypes.c_void_p]
@@ -153,9 +154,11 @@ class OracleSim:
     [, noise="uniform" | "gaussian"]); origin places this box inside a larger lattice for the nozzle
     mask and the noise counter (a sub-box that reproduces part of a full-size run).
     sponge = (W, K): viscosity raised over the last W layers towards z+ (jet exit).
+    forcing = "luo" (default) or "guo"; with Guo forcing and a force field, set the
+    field before init_moments (the initial populations depend on it).
     """
 
-    def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, inflow=None, sponge=None):
+    def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, inflow=None, sponge=None, forcing="luo"):
         self.dims = tuple(int(d) for d in dims)
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
         d = np.array(self.dims, dtype=np.int64)
@@ -180,6 +183,9 @@ class OracleSim:
         if sponge is not None:
             if lib().orc_set_sponge(self._h, int(sponge[0]), float(sponge[1])) != 0:
                 raise ValueError("oracle rejected the sponge layer")
+        if forcing != "luo":
+            if lib().orc_set_forcing(self._h, {"guo": 1}[forcing]) != 0:
+                raise ValueError("oracle rejected Guo forcing for these faces")
 
     def __del__(self):
         if getattr(self, "_h", None):

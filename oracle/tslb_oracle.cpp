@@ -48,6 +48,14 @@
 //       the same Philox4x32-10 block as the uniform noise:
 //       u1 = ((r0 >> 8) + 1) 2^-24 in (0, 1], u2 = (r1 >> 8) 2^-24,
 //       xi = sqrt(-2 ln u1) cos(2 pi u2).
+//   R11 Guo forcing (an alternative to the Luo term, selected per simulation):
+//       velocity u = (sum f c + rho F/2)/rho, stored stress
+//       Pi^G = sum f c c - rho u u - rho cs^2 delta + (rho/2)(u F + F u), and
+//       f^post = f^eq(rho, u) + (1-omega) f^neq(Pi^G, u) + F_i/2 with Guo's
+//       term F_i = w_i rho [(c - u).F / cs^2 + (c.u)(c.F) / cs^4] (the BGK
+//       update with (1 - omega/2) F_i, written with the non-equilibrium part
+//       f - f^eq + F/2 regularised).  Initial populations from given moments:
+//       f^eq + f^neq - F_i/2.  Defined for periodic and wall faces (no ghosts).
 //   R10 no-slip walls by the thread-safe non-equilibrium extrapolation
 //       (Sec. 2.3, Eq. neq_final with the imposed momentum u_B = 0): the wall
 //       sits on the boundary layer y = 0 (or ny-1), whose nodes emit
@@ -163,6 +171,21 @@ void moments(const T* f, T& rho, T u[3], T pi[3][3]) {
 
 // Post-collision populations of one node: Eq. LBexp with the third-order
 // Hermite pieces, plus the Luo forcing term rho w_i c_i.F/cs^2 (Sec. 3.1).
+// Guo's forcing term F_i = w_i rho [(c - u).F / cs^2 + (c.u)(c.F) / cs^4] (R11).
+template <class T>
+void guo_term(const T& rho, const T u[3], const T F[3], T out[27]) {
+    for (int i = 0; i < 27; ++i) {
+        const int* c = L.c[i];
+        T cmuF = 0.0, cu = 0.0, cF = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            cmuF += (double(c[a]) - u[a]) * F[a];
+            cu += double(c[a]) * u[a];
+            cF += double(c[a]) * F[a];
+        }
+        out[i] = L.w[i] * rho * (cmuF / CS2 + cu * cF / CS4);
+    }
+}
+
 template <class T>
 void post_collision(const T& rho, const T u[3], const T pi[3][3], double omega, const T F[3],
                     T out[27]) {
@@ -242,6 +265,7 @@ struct Sim {
     double omega;
     T F[3];
     bool has_field;
+    int forcing;  // 0: Luo term, 1: Guo (R11)
     std::vector<T> field;  // [3][N] per-node acceleration
     Inflow inflow;
     int64_t t;
@@ -274,6 +298,17 @@ struct Sim {
 template <class T>
 void node_moments(const Sim<T>& s, int64_t node, T& rho, T u[3], T pi[3][3]) {
     moments(&s.f[node * 27], rho, u, pi);
+    if (s.forcing == 1) {
+        // R11: u += F/2; Pi^G = sum f c c - rho u u - rho cs^2 delta + (rho/2)(u F + F u)
+        T F[3], m2[3][3];
+        s.force_at(node, F);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) m2[a][b] = pi[a][b] + rho * u[a] * u[b];  // sum f c c - rho cs^2 delta
+        for (int a = 0; a < 3; ++a) u[a] = u[a] + 0.5 * F[a];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                pi[a][b] = m2[a][b] - rho * u[a] * u[b] + 0.5 * rho * (u[a] * F[b] + F[a] * u[b]);
+    }
 }
 
 // Post-collision populations emitted by source node (x,y,z): an interior node,
@@ -315,6 +350,15 @@ void source_post(const Sim<T>& s, int64_t x, int64_t y, int64_t z, T out[27]) {
     int64_t node = s.idx(x, y, zs);
     node_moments(s, node, rho, u, pi);
     s.force_at(node, F);
+    if (s.forcing == 1) {
+        T eq[27], neq[27], gF[27];
+        feq3(rho, u, eq);
+        fneq3(pi, u, neq);
+        guo_term(rho, u, F, gF);
+        const double w = s.omega_at(z);
+        for (int i = 0; i < 27; ++i) out[i] = eq[i] + (1.0 - w) * neq[i] + 0.5 * gF[i];
+        return;
+    }
     post_collision(rho, u, pi, s.omega_at(z), F, out);
 }
 
@@ -412,6 +456,7 @@ int validate_and_init(Sim<T>* s, const int64_t dims[3], double tau, const double
     s->t = 0;
     s->sponge_w = 0;
     s->sponge_k = 0.0;
+    s->forcing = 0;
     s->f.assign(s->N() * 27, T(0.0));
     s->fnew.assign(s->N() * 27, T(0.0));
     return 0;
@@ -439,6 +484,12 @@ void init_from_moments(Sim<T>* s, const T* rho, const T* u, const T* pi) {
                 feq3(r, uu, eq);
                 fneq3(p, uu, neq);
                 for (int i = 0; i < 27; ++i) s->f[node * 27 + i] = eq[i] + neq[i];
+                if (s->forcing == 1) {  // R11: the populations whose moments are the given state
+                    T F[3], gF[27];
+                    s->force_at(node, F);
+                    guo_term(r, uu, F, gF);
+                    for (int i = 0; i < 27; ++i) s->f[node * 27 + i] -= 0.5 * gF[i];
+                }
             }
     s->t = 0;
 }
@@ -515,6 +566,15 @@ void* orc_create(const int64_t* dims, double tau, const double* F, const int* bc
     return s;
 }
 void orc_destroy(void* h) { delete static_cast<Sim<double>*>(h); }
+// Forcing scheme: 0 = Luo term, 1 = Guo (R11; periodic and wall faces only).
+int orc_set_forcing(void* h, int kind) {
+    Sim<double>* s = static_cast<Sim<double>*>(h);
+    if (kind != 0 && kind != 1) return -1;
+    for (int f = 0; f < 6; ++f)
+        if (kind == 1 && (s->bc[f] == BC_INFLOW || s->bc[f] == BC_OUTFLOW || s->bc[f] == BC_NEE_WALL)) return -1;
+    s->forcing = kind;
+    return 0;
+}
 // Sponge layer of width W (0: none) and strength K along the z+ end (R8).
 int orc_set_sponge(void* h, int64_t width, double k) {
     Sim<double>* s = static_cast<Sim<double>*>(h);

@@ -319,6 +319,72 @@ def test_poiseuille_nee_walls_second_order():
     assert math.log2(e8 / e16) > 1.8 and math.log2(e16 / e32) > 1.8
 
 
+def test_guo_forcing_uniform_acceleration():
+    """Guo forcing (reading of the forcing alternative): a uniform flow under a
+    constant acceleration stays uniform with u(t) = u0 + F t exactly and no
+    non-equilibrium stress, because Guo's term carries the second moment
+    rho (u F + F u) that the acceleration of rho u u requires; the Luo term of
+    Sec. 3.1 leaves a spurious stress of order rho u F instead."""
+    dims, N = (4, 5, 3), 60
+    U = np.array([0.02, -0.01, 0.005])
+    F = np.array([1e-4, 2e-4, -3e-4])
+    res = {}
+    for forcing in ("guo", "luo"):
+        s = oracle.OracleSim(dims, 0.7, force=F, forcing=forcing)
+        s.init_moments(np.ones(N) * 1.02, np.tile(U[:, None], (1, N)))
+        s.step(5)
+        r, u, p = s.get_moments()
+        assert np.abs(u - (U + 5 * F)[:, None]).max() < 1e-15
+        res[forcing] = np.abs(p).max()
+    assert res["guo"] < 1e-15
+    assert res["luo"] > 1e-6
+
+
+def test_guo_forcing_momentum_growth():
+    """Guo forcing: the momentum of the stored state, sum rho u with u the
+    half-force-shifted velocity, grows by F times the mass every step."""
+    dims = (5, 4, 6)
+    rho, u, pi = W.random_state(dims, seed=4)
+    F = np.array([2e-6, -1e-6, 3e-6])
+    s = oracle.OracleSim(dims, 0.7, force=F, forcing="guo")
+    s.init_moments(rho, u, pi)
+    r0, u0, _ = s.get_moments()
+    assert np.abs(u0 - u).max() < 1e-15 and np.abs(r0 - rho).max() < 1e-15  # the state is stored as given
+    M = rho.sum()
+    P0 = (rho[None, :] * u).sum(1)
+    s.step(20)
+    r, uu, _ = s.get_moments()
+    assert abs(r.sum() - M) / M < 1e-13
+    assert np.abs((r[None, :] * uu).sum(1) - (P0 + 20 * F * M)).max() < 1e-13
+
+
+@pytest.mark.slow
+def test_guo_forcing_poiseuille_second_order():
+    """Guo forcing between halfway bounce-back walls: second-order convergence to the parabola."""
+    def err(H, tau=0.8, g=1e-6):
+        ny = H + 2
+        dims = (3, ny, 3)
+        N = 3 * ny * 3
+        nu = CS2 * (tau - 0.5)
+        y = np.tile(np.repeat(np.arange(ny, dtype=float), 3), 3)
+        y0, y1 = 0.5, ny - 1.5
+        exact = g / (2 * nu) * (y - y0) * (y1 - y)
+        fluid = (y >= 1) & (y <= ny - 2)
+        u = np.zeros((3, N))
+        u[0] = np.where(fluid, exact, 0.0)
+        pi = np.zeros((6, N))
+        pi[3] = np.where(fluid, -CS2 * tau * g / (2 * nu) * (y1 + y0 - 2 * y), 0.0)
+        s = oracle.OracleSim(dims, tau, force=(g, 0, 0), bc=(0, 0, 1, 1, 0, 0), forcing="guo")
+        s.init_moments(np.ones(N), u, pi)
+        s.step(int(3 * H * H / nu))
+        _, uu, _ = s.get_moments()
+        e = uu[0][fluid] - exact[fluid]
+        return np.sqrt(np.mean(e ** 2)) / np.sqrt(np.mean(exact[fluid] ** 2))
+    e8, e16, e32 = err(8), err(16), err(32)
+    assert e8 < 0.05
+    assert math.log2(e8 / e16) > 1.8 and math.log2(e16 / e32) > 1.8
+
+
 def test_freeslip_neumann_mode_decay():
     """u_x = A cos(pi (y - 1/2) / H) between free-slip walls at y = 1/2, H + 1/2 decays at nu (pi/H)^2."""
     H, tau, A = 32, 0.8, 0.01
