@@ -84,6 +84,17 @@ typedef enum tslb_precision {
 
 typedef enum tslb_where { TSLB_HOST = 0, TSLB_DEVICE = 1 } tslb_where;
 
+/* Body-force schemes.  TSLB_FORCING_LUO is the paper's term rho w_i c_i.F/cs^2
+ * added to the post-collision populations (Sec. 3.1).  TSLB_FORCING_GUO is Guo's
+ * scheme: the stored velocity is u = (sum f c + rho F/2)/rho, the stored stress
+ * is Pi = sum f c c - rho u u - rho cs^2 delta + (rho/2)(u F + F u), and the
+ * post-collision populations are f^eq + (1 - omega) f^neq(Pi) + F_i/2 with
+ * F_i = w_i rho [(c - u).F/cs^2 + (c.u)(c.F)/cs^4]; a uniformly accelerating
+ * flow then carries no spurious stress.  Guo forcing needs TSLB_D3Q27 with
+ * periodic x and z faces, y faces periodic, bounce-back or free-slip, no sponge
+ * layer, and is not supported by tslb_adjoint_force_gradient. */
+typedef enum tslb_forcing { TSLB_FORCING_LUO = 0, TSLB_FORCING_GUO = 1 } tslb_forcing;
+
 typedef enum tslb_kernel {
     TSLB_KERNEL_AUTO = 0,     /* the fastest kernel that supports the configuration */
     TSLB_KERNEL_DIRECT = 1,   /* one thread per node, 27 direct gathers (cross-check path) */
@@ -130,6 +141,7 @@ typedef struct tslb_options {
      * W < nz and sponge_k >= 0; not supported by tslb_adjoint_force_gradient. */
     int sponge_width;
     double sponge_k;
+    int forcing;          /* tslb_forcing, default TSLB_FORCING_LUO */
 } tslb_options;
 
 typedef struct tslb_diag {

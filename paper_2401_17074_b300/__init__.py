@@ -28,6 +28,7 @@ FP32, BF16, FP16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED = 0, 1, 2
 TSLB_NOISE_UNIFORM, TSLB_NOISE_GAUSSIAN = 0, 1
+TSLB_FORCING_LUO, TSLB_FORCING_GUO = 0, 1
 
 EXPORTED = [
     "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_set_force_field", "tslb_step",
@@ -46,7 +47,7 @@ class tslb_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("u_ref", ctypes.c_double), ("pi_ref", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("checkpoint_every", ctypes.c_int), ("inflow", tslb_inflow), ("sponge_width", ctypes.c_int),
-                ("sponge_k", ctypes.c_double)]
+                ("sponge_k", ctypes.c_double), ("forcing", ctypes.c_int)]
 
 
 class tslb_diag(ctypes.Structure):
@@ -233,7 +234,7 @@ class Solver:
 
     def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05, pi_ref=1e-3,
                  kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None, sponge=None,
-                 lattice=None):
+                 lattice=None, forcing="luo"):
         """inflow: dict(center2, diameter, u_jet, noise_amp, seed[, noise="uniform" | "gaussian"]);
         sponge: (width, K) viscosity layer towards the z+ face (tslb_options.sponge_width / sponge_k)."""
         o = tslb_options_default()
@@ -254,6 +255,7 @@ class Solver:
             o.inflow.seed = int(inflow["seed"])
             o.inflow.noise_kind = {"uniform": TSLB_NOISE_UNIFORM,
                                    "gaussian": TSLB_NOISE_GAUSSIAN}[inflow.get("noise", "uniform")]
+        o.forcing = {"luo": TSLB_FORCING_LUO, "guo": TSLB_FORCING_GUO}[forcing]
         if sponge is not None:
             o.sponge_width = int(sponge[0])
             o.sponge_k = float(sponge[1])

@@ -100,6 +100,7 @@ Physics make_physics(const tslb_s* h) {
     p.in_seed = h->inflow.seed;
     p.in_gauss = h->inflow.noise_kind == TSLB_NOISE_GAUSSIAN ? 1 : 0;
     p.omega1_z = h->omega1_z;
+    p.guo = h->forcing == TSLB_FORCING_GUO ? 1 : 0;
     p.t = h->t;
     p.err = h->dev_err;
     p.drop_row = inject_exchange_fault() ? 5 : -1;
@@ -199,6 +200,12 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     if (bz0 == TSLB_BC_INFLOW && o.inflow.diameter < 0) return fail(nullptr, TSLB_ERR_INVALID, "bad inflow diameter");
     if (d2 && (bx != TSLB_BC_PERIODIC || !(by == TSLB_BC_PERIODIC || by == TSLB_BC_BOUNCEBACK)))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "D2Q9: periodic x, periodic or bounce-back y");
+    if (o.forcing != TSLB_FORCING_LUO && o.forcing != TSLB_FORCING_GUO)
+        return fail(nullptr, TSLB_ERR_INVALID, "unknown forcing scheme");
+    if (o.forcing == TSLB_FORCING_GUO &&
+        (d2 || bx != TSLB_BC_PERIODIC || bz0 != TSLB_BC_PERIODIC || by == TSLB_BC_NEE_WALL || o.sponge_width != 0))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED,
+                    "Guo forcing: D3Q27, periodic x and z, no NEE walls, no sponge layer");
     if (d2 && (o.precision != TSLB_FP32 || o.checkpoint_every != 0 || o.sponge_width != 0))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "D2Q9: FP32 storage, no checkpoints, no sponge layer");
     if (o.inflow.noise_kind != TSLB_NOISE_UNIFORM && o.inflow.noise_kind != TSLB_NOISE_GAUSSIAN)
@@ -227,6 +234,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     h->checkpoint_every = o.checkpoint_every;
     h->inflow = o.inflow;
     h->sponge_width = o.sponge_width;
+    h->forcing = o.forcing;
     h->sponge_k = o.sponge_k;
     h->elem = o.precision == TSLB_FP32 ? 4 : 2;
 
@@ -486,6 +494,7 @@ int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int wher
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
     if (h->omega1_z) return fail(h, TSLB_ERR_UNSUPPORTED, "the adjoint does not support a sponge layer");
     if (h->lattice == TSLB_D2Q9) return fail(h, TSLB_ERR_UNSUPPORTED, "the adjoint is implemented for D3Q27");
+    if (h->forcing != TSLB_FORCING_LUO) return fail(h, TSLB_ERR_UNSUPPORTED, "the adjoint is implemented for Luo forcing");
     cudaSetDevice(h->device);
     std::string msg;
     const int r = tslb::adjoint_force_gradient(h, nsteps, dJdF, where, &msg);

@@ -67,6 +67,7 @@ struct Physics {
     float in_amp;
     unsigned long long in_seed;
     int in_gauss;          // Gaussian (Box-Muller) instead of uniform inflow noise
+    int guo;               // Guo forcing instead of the Luo term
     long long t;           // step index of the state being read
     int* err;              // device status word (nonzero: a kernel gave up a bounded wait)
     int drop_row;          // test hook: warp row of the factored step that withholds its exchange arrival (-1: none)
@@ -255,9 +256,12 @@ constexpr float CS2 = 1.0f / 3.0f;
 // Mode coefficients (deviation form) of the post-collision population.
 // (rho-1, u) enter the equilibrium part, (v, Pi) the non-equilibrium part
 // (v = u everywhere except the inflow ghost layer of Eq. neq_final).
+// With guo set, (jx_add, jy_add, jz_add) is the acceleration F of Guo's
+// forcing: j = rho (u + F/2) and h2 gains (rho/2)(u F + F u); otherwise it is
+// the Luo term's F, j = rho (u + F).
 __device__ __forceinline__ void post_modes(float drho, float ux, float uy, float uz, float vx, float vy, float vz,
                                            const float pi[6], float jx_add, float jy_add, float jz_add,
-                                           float omega1, float A[NMODES]) {
+                                           float omega1, float A[NMODES], bool guo = false) {
     const float rho = 1.0f + drho;
     const float pxx = omega1 * pi[0], pyy = omega1 * pi[1], pzz = omega1 * pi[2];
     const float pxy = omega1 * pi[3], pxz = omega1 * pi[4], pyz = omega1 * pi[5];
@@ -273,16 +277,18 @@ __device__ __forceinline__ void post_modes(float drho, float ux, float uy, float
     const float h3xzz = fmaf(qxz, uz, fmaf(2.0f * vz, pxz, vx * pzz));
     const float h3yzz = fmaf(qyz, uz, fmaf(2.0f * vz, pyz, vy * pzz));
     const float h3xyz = fmaf(qxy, uz, fmaf(vx, pyz, fmaf(vy, pxz, vz * pxy)));
+    const float jf = guo ? 0.5f : 1.0f;
+    const float gm = guo ? 1.0f : 0.0f, gh = 0.5f * gm;
     A[M000] = drho;
-    A[M100] = 3.0f * fmaf(rho, jx_add, rux);
-    A[M010] = 3.0f * fmaf(rho, jy_add, ruy);
-    A[M001] = 3.0f * fmaf(rho, jz_add, ruz);
-    A[M200] = 1.5f * h2xx;
-    A[M020] = 1.5f * h2yy;
-    A[M002] = 1.5f * h2zz;
-    A[M110] = 9.0f * h2xy;
-    A[M101] = 9.0f * h2xz;
-    A[M011] = 9.0f * h2yz;
+    A[M100] = 3.0f * fmaf(rho * jf, jx_add, rux);
+    A[M010] = 3.0f * fmaf(rho * jf, jy_add, ruy);
+    A[M001] = 3.0f * fmaf(rho * jf, jz_add, ruz);
+    A[M200] = 1.5f * fmaf(gm * rux, jx_add, h2xx);
+    A[M020] = 1.5f * fmaf(gm * ruy, jy_add, h2yy);
+    A[M002] = 1.5f * fmaf(gm * ruz, jz_add, h2zz);
+    A[M110] = 9.0f * fmaf(gh, fmaf(rux, jy_add, ruy * jx_add), h2xy);
+    A[M101] = 9.0f * fmaf(gh, fmaf(rux, jz_add, ruz * jx_add), h2xz);
+    A[M011] = 9.0f * fmaf(gh, fmaf(ruy, jz_add, ruz * jy_add), h2yz);
     A[M210] = 4.5f * h3xxy;
     A[M201] = 4.5f * h3xxz;
     A[M120] = 4.5f * h3xyy;
@@ -335,6 +341,22 @@ __device__ __forceinline__ float rcp_refined(float r) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(i) : "f"(r));
     const float e = fmaf(-r, i, 1.0f);
     return fmaf(i, e, i);
+}
+
+// Guo forcing's part of the new moments (F the acceleration at the node):
+// u = J/(216 + D0) + F/2 and Pi^G = (S - J u - delta D0/3)/216 + rho F F/4
+// (pi_scale converts Pi to the units out[] holds it in).
+__device__ __forceinline__ void guo_finish(float out[NFIELDS], float F0, float F1, float F2, float pi_scale) {
+    const float q = 0.25f * (1.0f + out[F_DRHO]) * pi_scale;
+    out[F_UX] = fmaf(0.5f, F0, out[F_UX]);
+    out[F_UY] = fmaf(0.5f, F1, out[F_UY]);
+    out[F_UZ] = fmaf(0.5f, F2, out[F_UZ]);
+    out[F_PXX] = fmaf(q * F0, F0, out[F_PXX]);
+    out[F_PYY] = fmaf(q * F1, F1, out[F_PYY]);
+    out[F_PZZ] = fmaf(q * F2, F2, out[F_PZZ]);
+    out[F_PXY] = fmaf(q * F0, F1, out[F_PXY]);
+    out[F_PXZ] = fmaf(q * F0, F2, out[F_PXZ]);
+    out[F_PYZ] = fmaf(q * F1, F2, out[F_PYZ]);
 }
 
 __device__ __forceinline__ void finish_moments(float D0, const float J[3], const float S[6], float out[NFIELDS]) {
@@ -422,6 +444,7 @@ struct tslb_s {
     int sponge_width = 0;
     double sponge_k = 0.0;
     float* omega1_z = nullptr;  // sponge layer table, (1 - omega) per full-lattice z
+    int forcing = TSLB_FORCING_LUO;
     size_t elem = 4;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;

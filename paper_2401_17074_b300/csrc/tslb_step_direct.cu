@@ -32,7 +32,7 @@ __device__ __forceinline__ void node_modes(const typename Codec::T* __restrict__
         F2 = p.force[2 * g.fstride + idx];
     }
     post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
-               omega1_at(p, zfull), A);
+               omega1_at(p, zfull), A, p.guo != 0);
 }
 
 template <class Codec>
@@ -121,6 +121,15 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
     // New moments (Sec. 2.1) from the 216-scaled deviation sums.
     float out[NFIELDS];
     finish_moments(D0, J, S, out);
+    if (p.guo) {
+        float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
+        if (p.force) {
+            F0 = p.force[n];
+            F1 = p.force[g.fstride + n];
+            F2 = p.force[2 * g.fstride + n];
+        }
+        guo_finish(out, F0, F1, F2, 1.0f);
+    }
     NodeIO<Codec>::store(dst, g.fstride, n, p, out);
 }
 

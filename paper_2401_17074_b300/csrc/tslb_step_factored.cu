@@ -226,6 +226,9 @@ __device__ __forceinline__ HermP to_pairs(const Herm& h) {
 // + 2 P_ab), the third-order terms are h3_aab = u_a t_ab + u_b P_aa and
 // h3_xyz = rho u_x u_y u_z + u_x P_yz + u_y P_xz + u_z P_xy.  The x and y
 // components run as pairs.
+// GUO: Guo forcing (j = rho (u + F/2), h2 += (rho/2)(u F + F u)) instead of
+// the Luo term (j = rho (u + F)).
+template <bool GUO>
 __device__ __forceinline__ HermP hermite_p(float drho, float ux, float uy, float uz, const float pi[6], float Fx,
                                            float Fy, float Fz, float omega1) {
     HermP q;
@@ -238,8 +241,9 @@ __device__ __forceinline__ HermP hermite_p(float drho, float ux, float uy, float
     const f2 ruxy = mul2(rho2, uxy);
     const float ruz = rho * uz;
     q.drho = drho;
-    q.jxy = fma2(rho2, make_float2(Fx, Fy), ruxy);
-    q.jz = fmaf(rho, Fz, ruz);
+    const float jf = GUO ? 0.5f : 1.0f;
+    q.jxy = fma2(rho2, make_float2(jf * Fx, jf * Fy), ruxy);
+    q.jz = fmaf(rho, jf * Fz, ruz);
     q.h2d = fma2(ruxy, uxy, Pd);
     q.zz = fmaf(ruz, uz, Pzy.x);
     const f2 qz = mul2(ruxy, uz2);  // (rho u_x u_z, rho u_y u_z)
@@ -252,6 +256,12 @@ __device__ __forceinline__ HermP hermite_p(float drho, float ux, float uy, float
     q.h3z = fma2(uxy, tz, mul2(uz2, Pd));          // (h_xxz, h_yyz)
     q.h3y = make_float2(fmaf(ux, txy, uy * Pd.x), fmaf(uy, txy, ux * Pd.y));
     q.xyz = fmaf(qxy, uz, fmaf(ux, Pq.y, fmaf(uy, Pq.x, uz * Pzy.y)));
+    if (GUO) {  // after the third-order terms, which take h2 without it
+        q.h2d = fma2(ruxy, make_float2(Fx, Fy), q.h2d);
+        q.zz = fmaf(ruz, Fz, q.zz);
+        q.h2z = fma2(k2(0.5f), fma2(ruxy, k2(Fz), mul2(make_float2(Fx, Fy), k2(ruz))), q.h2z);
+        q.xy = fmaf(0.5f, fmaf(ruxy.x, Fy, ruxy.y * Fx), q.xy);
+    }
     return q;
 }
 
@@ -310,7 +320,7 @@ struct Ctx {
     int offLv, offRv, offLs, offRs;  // y-exchange read offsets (float4 / float units, relative to a slot base)
 };
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO>
 struct Kernel {
     typedef typename Codec::T T;
 
@@ -382,7 +392,7 @@ struct Kernel {
             } else {
                 float F0, F1, F2;
                 load_force(p, g, idx, F0, F1, F2);
-                h = hermite_p(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, om_pi);
+                h = hermite_p<GUO>(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, om_pi);
             }
             zpops(h, P);
         }
@@ -515,6 +525,11 @@ struct Kernel {
                     out[F_PYZ] = (S[5] - J[1] * uz) * ps;
                 }
                 const unsigned oidx = c.col + c.plane * (unsigned)(zs - 1);
+                if (GUO) {
+                    float G0, G1, G2;
+                    load_force(p, g, oidx, G0, G1, G2);
+                    guo_finish(out, G0, G1, G2, sizeof(T) == 4 ? 1.0f : p.inv_s_pi);
+                }
                 if (c.store) NodeIO<Codec>::store_rawpi(dst, g.fstride, oidx, p, out);
             }
         }
@@ -547,7 +562,8 @@ struct Kernel {
     static __device__ __forceinline__ void bounce_back_correction(const float m[NFIELDS], float F0, float F1, float F2,
                                                                   float omega1, float s, float* out) {
         float Ao[NMODES];
-        post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, omega1, Ao);
+        post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, omega1, Ao,
+                   GUO);
         const float B00 = fmaf(2.0f, Ao[M020], fmaf(-s, Ao[M010], Ao[M000]));
         const float B10 = fmaf(2.0f, Ao[M120], fmaf(-s, Ao[M110], Ao[M100]));
         const float B01 = fmaf(2.0f, Ao[M021], fmaf(-s, Ao[M011], Ao[M001]));
@@ -576,11 +592,11 @@ struct Kernel {
     }
 };
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO>
 __global__ void __launch_bounds__(NT, 1)
     step_factored_kernel(const typename Codec::T* __restrict__ src, typename Codec::T* __restrict__ dst, Geometry g,
                          Physics p, int zchunk) {
-    typedef Kernel<Codec, XFREE, SPONGE, NEEY> K;
+    typedef Kernel<Codec, XFREE, SPONGE, NEEY, GUO> K;
     extern __shared__ __align__(16) float ysm[];  // [2][YBUF] y exchange, then [2][PF::BUF] plane prefetch
     char* pfb = reinterpret_cast<char*>(ysm) + 2 * YBUF;
     float* corr = reinterpret_cast<float*>(pfb + 2 * K::PF::BUF);
@@ -649,9 +665,9 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO>
 cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY>;
+    auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY, GUO>;
     static bool configured[64] = {};
     const int dev = h->device;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -690,12 +706,17 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
 template <class Codec>
 cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Physics& p) {
     const bool xfree = h->g.bc[0] == TSLB_BC_FREESLIP, sponge = p.omega1_z != nullptr;
-    // NEE y walls come with periodic x (checked at create)
+    // Guo forcing comes with periodic x, no sponge and no NEE walls; NEE y walls
+    // with periodic x (both checked at create)
+    if (p.guo) return launch_t<Codec, false, false, false, true>(h, src, dst, p);
     if (h->g.bc[2] == TSLB_BC_NEE_WALL)
-        return sponge ? launch_t<Codec, false, true, true>(h, src, dst, p) : launch_t<Codec, false, false, true>(h, src, dst, p);
+        return sponge ? launch_t<Codec, false, true, true, false>(h, src, dst, p)
+                      : launch_t<Codec, false, false, true, false>(h, src, dst, p);
     if (xfree)
-        return sponge ? launch_t<Codec, true, true, false>(h, src, dst, p) : launch_t<Codec, true, false, false>(h, src, dst, p);
-    return sponge ? launch_t<Codec, false, true, false>(h, src, dst, p) : launch_t<Codec, false, false, false>(h, src, dst, p);
+        return sponge ? launch_t<Codec, true, true, false, false>(h, src, dst, p)
+                      : launch_t<Codec, true, false, false, false>(h, src, dst, p);
+    return sponge ? launch_t<Codec, false, true, false, false>(h, src, dst, p)
+                  : launch_t<Codec, false, false, false, false>(h, src, dst, p);
 }
 
 }  // namespace

@@ -123,6 +123,23 @@ def test_d2q9_create_rules():
     assert c == T.TSLB_ERR_UNSUPPORTED
 
 
+def test_guo_forcing_rules():
+    for kw in (dict(bc=(2, 2, 0, 0, 0, 0)), dict(bc=(0, 0, 5, 5, 0, 0)), dict(bc=(0, 0, 0, 0, 3, 4), dims=(8, 8, 8)),
+               dict(dims=(8, 8, 1), lattice=T.TSLB_D2Q9)):
+        o = T.tslb_options_default()
+        o.forcing = T.TSLB_FORCING_GUO
+        c, h = _create_code(opt=o, **kw)
+        assert c == T.TSLB_ERR_UNSUPPORTED, kw
+    o = T.tslb_options_default()
+    o.forcing = T.TSLB_FORCING_GUO
+    o.sponge_width = 3
+    o.sponge_k = 1.0
+    assert _create_code(opt=o)[0] == T.TSLB_ERR_UNSUPPORTED
+    o = T.tslb_options_default()
+    o.forcing = 7
+    assert _create_code(opt=o)[0] == T.TSLB_ERR_INVALID
+
+
 def test_null_handle_calls_fail_cleanly():
     L = T.load()
     assert L.tslb_step(None, 1) == T.TSLB_ERR_INVALID

@@ -47,14 +47,15 @@ def rel_errors(gpu, ref, mask):
 
 
 def run_pair(dims, tau, state, nsteps, kernel, bc=(0,) * 6, force=(0.0, 0.0, 0.0), inflow=None, precision=T.FP32,
-             force_field=None, sponge=None):
-    o = oracle.OracleSim(dims, tau, force=force, bc=bc, inflow=inflow, sponge=sponge)
-    o.init_moments(*state)
-    if force_field is not None:
+             force_field=None, sponge=None, forcing="luo"):
+    o = oracle.OracleSim(dims, tau, force=force, bc=bc, inflow=inflow, sponge=sponge, forcing=forcing)
+    if force_field is not None:  # before the moments: Guo's initial populations depend on it
         o.set_force_field(force_field.astype(np.float64))
+    o.init_moments(*state)
     o.step(nsteps)
     ref = stack(*o.get_moments())
-    s = T.Solver(dims, tau, force=force, bc=bc, kernel=kernel, inflow=inflow, precision=precision, sponge=sponge)
+    s = T.Solver(dims, tau, force=force, bc=bc, kernel=kernel, inflow=inflow, precision=precision, sponge=sponge,
+                 forcing=forcing)
     s.init_moments(*state)
     if force_field is not None:
         s.set_force_field(force_field.astype(np.float32))
@@ -201,6 +202,49 @@ def test_sponge_with_periodic_z(cuda_ok, kernel):
     state = W.random_state(dims, seed=29, drho=0.002, du=0.01, dpi=1e-4)
     errs, _, _ = run_pair(dims, 0.6, state, 6, kernel, sponge=(6, 5.0))
     assert_all_below(errs, 3e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("bc", [(0,) * 6, (0, 0, 1, 1, 0, 0), (0, 0, 2, 2, 0, 0)], ids=["periodic", "bounce-back", "free-slip"])
+def test_guo_forcing(cuda_ok, kernel, bc):
+    """Guo forcing: half-force velocity, corrected stress, F_i/2 in the update."""
+    dims = (33, 20, 6)
+    state = W.random_state(dims, seed=31)
+    errs, _, _ = run_pair(dims, 0.6, state, 5, kernel, bc=bc, force=(3e-5, -2e-5, 1e-5), forcing="guo")
+    assert_all_below(errs, 3e-6)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec", [T.FP32, T.BF16], ids=["fp32", "bf16"])
+def test_guo_forcing_field(cuda_ok, kernel, prec):
+    """Guo forcing with a per-node acceleration field (FP32 and 16-bit storage)."""
+    dims = (12, 10, 7)
+    state = W.random_state(dims, seed=32)
+    rng = np.random.default_rng(33)
+    F = (2e-5 * rng.uniform(-1, 1, (3, dims[0] * dims[1] * dims[2])))
+    errs, _, _ = run_pair(dims, 0.7, state, 4, kernel, force_field=F, forcing="guo", precision=prec)
+    assert_all_below(errs, 3e-6 if prec == T.FP32 else 5e-3)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_guo_forced_channel(cuda_ok, kernel):
+    """The forced channel with Guo forcing at the bench relaxation time, 30 steps."""
+    prm = W.channel_params(nx=40, ny=34, nz=20)
+    state = W.channel_state(prm, seed=2)
+    errs, _, _ = run_pair(prm["dims"], prm["tau"], state, 30, kernel, bc=prm["bc"], force=prm["force"],
+                          forcing="guo")
+    assert errs["ux"] <= 1e-5, errs
+    assert_all_below(errs, 1e-4)
+
+
+def test_guo_adjoint_rejected(cuda_ok):
+    s = T.Solver((8, 8, 8), 0.6, force=(1e-5, 0, 0), forcing="guo", checkpoint_every=2)
+    s.init_moments(np.ones(512), np.zeros((3, 512)))
+    s.step(2)
+    with pytest.raises(T.TslbError) as ei:
+        s.adjoint_force_gradient(2)
+    assert ei.value.code == T.TSLB_ERR_UNSUPPORTED
+    s.close()
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
