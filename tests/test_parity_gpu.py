@@ -248,6 +248,26 @@ def test_guo_adjoint_rejected(cuda_ok):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec", [T.BF16, T.FP16], ids=["bf16", "fp16"])
+@pytest.mark.parametrize("case", ["nee-walls", "paper-jet"])
+def test_16bit_storage_faces(cuda_ok, kernel, prec, case):
+    """16-bit storage with the NEE walls and with the paper's jet faces (sponge,
+    Gaussian inflow noise).  Each stored value is rounded once per step to
+    eps = 2^-9 (BF16) or 2^-12 (FP16) of its scale; a wrong face would show as
+    O(0.1 - 1) errors on its rows, the bound 2e-2 is about ten BF16 roundings."""
+    if case == "nee-walls":
+        dims, bc = (33, 18, 6), (0, 0, 5, 5, 0, 0)
+        state = W.random_state(dims, seed=34)
+        errs, _, _ = run_pair(dims, 0.6, state, 3, kernel, bc=bc, force=(2e-5, 0.0, 0.0), precision=prec)
+    else:
+        dims, bc = (34, 24, 40), (0, 0, 0, 0, 3, 4)
+        inflow = dict(center2=(33, 23), diameter=8, u_jet=0.05, noise_amp=0.01, seed=3, noise="gaussian")
+        state = W.random_state(dims, seed=35, drho=0.002, du=0.01, dpi=1e-4)
+        errs, _, _ = run_pair(dims, 0.52, state, 10, kernel, bc=bc, inflow=inflow, sponge=(10, 1000.0), precision=prec)
+    assert_all_below(errs, 2e-2)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_force_field(cuda_ok, kernel):
     dims = (6, 5, 4)
     state = W.random_state(dims, seed=26)
