@@ -74,9 +74,9 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_record(kernel_name, precision):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel sources are unchanged since."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+def profile_record(fname, kernel_name, precision, key):
+    """`key` of a committed ncu record under profiles/, if the kernel sources are unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -92,8 +92,30 @@ def traffic_record(kernel_name, precision):
             h.update(open(path, "rb").read())
         if h.hexdigest() != r.get("sources_sha256"):
             return None
-        return float(r["bytes_per_launch_full"])
+        return float(r[key])
     return None
+
+
+def traffic_record(kernel_name, precision):
+    """DRAM bytes per launch from a committed ncu capture."""
+    return profile_record("traffic.json", kernel_name, precision, "bytes_per_launch_full")
+
+
+FP32_LANES_PER_SM = 128
+NOMINAL_SM_MHZ = 2032.0
+
+
+def alu_entry(kernel_name, nodes, launch_s, sms, sm_mhz):
+    """Executed FP32 FLOP/s of the step against the CUDA-core FP32 peak (SMs x 128 lanes x 2 FLOP x clock).
+    FLOP per node come from committed ncu op counts (FFMA 2, packed FADD2/FMUL2 2, FFMA2 4); null when stale."""
+    fpn = profile_record("fp32_ops.json", kernel_name, "fp32", "fp32_flop_per_node")
+    if fpn is None:
+        return None
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = fpn * nodes / launch_s / 1e12
+    return {"bound": "alu", "flop_per_node": fpn, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_basis": "%d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz"
+            % (sms, FP32_LANES_PER_SM, sm_mhz), "kernel": kernel_name}
 
 
 class ClockSampler:
@@ -331,6 +353,9 @@ def time_channel2d(T, torch, stream, hbm, steps=500, warmup=20):
             "value": job_mlups(nodes, 1, steps, ms), "unit": "MLUPS", "steps": steps, "ms_per_step": ms / steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "algorithmic_bytes_per_node": 48, "kernel": "tslb_step2d"},
+            "alu": alu_entry("tslb_step2d", nodes, ms * 1e-3 / steps,
+                             torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count,
+                             NOMINAL_SM_MHZ),
             "status": code}
 
 
@@ -430,6 +455,8 @@ def main():
     from paper_2401_17074_b300 import build as B
     kname = "tslb_step_direct" if kernel == T.KERNEL_DIRECT else "tslb_step_factored"
     traffic = traffic_record(kname, args.precision)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu = alu_entry(kname, nodes, launch_s, sms, NOMINAL_SM_MHZ) if args.precision == "fp32" else None
 
     variants = {}
     if not args.no_variants:
@@ -445,8 +472,6 @@ def main():
             if fin is not None:
                 variants[prec]["error_vs_fp32_after_%d_steps" % (args.steps + args.warmup)] = \
                     precision_errors(prm, ref_final, fin)
-        if args.precision != "fp32":
-            pass
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = time_e2e(T, torch, prm, state, args.steps, stream)
@@ -482,10 +507,14 @@ def main():
                                                                   prm["force"][0], args.precision),
                        "interior_nodes": nodes, "storage": args.precision,
                        "l2": "inputs larger than L2: two %.0f MB moment buffers" % (bpn / 2 * nodes / 1e6),
-                       "parallelism": "replicas" if ws > 1 else "single GPU", "kernel": kname},
+                       "parallelism": "replicas" if ws > 1 else "single GPU", "kernel": kname,
+                       "paper_form": "MLUPS = nx ny nz steps / (1e6 T) over interior nodes: %d x %d x %d x %d / "
+                                     "(1e6 x %.4f s)" % (args.nx, prm["dims"][1] - 2, args.nz, args.steps,
+                                                          ms * 1e-3)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": traffic, "peak_source": hbm_src,
                          "algorithmic_bytes_per_node": bpn, "kernel": kname},
+            "alu": alu,
             "variants": variants,
             "e2e": e2e,
             "gpu_launches": args.steps,
