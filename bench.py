@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workload lines")
+    ap.add_argument("--no-precision-study", action="store_true",
+                    help="skip the time-averaged FP32 / BF16 / FP16 channel statistics")
     ap.add_argument("--only", default=None, choices=["d2q9"], help="time one extra workload alone (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -255,10 +257,12 @@ def job_mlups(nodes_per_rank, world_size, steps, ms):
     return nodes_per_rank * world_size * steps / (ms * 1e-3) / 1e6
 
 
-def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, dist, clocks=None, keep=False):
+def time_device(T, torch, prm, state, precision, kernel, steps, warmup, stream, dist, clocks=None, keep=False,
+                rounding="nearest"):
     from paper_2401_17074_b300 import workloads as W
     s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], precision=PREC_CODE[precision],
-                 kernel=kernel, stream=stream.cuda_stream, u_ref=0.05, pi_ref=W.pi_reference(state))
+                 kernel=kernel, stream=stream.cuda_stream, u_ref=0.05, pi_ref=W.pi_reference(state),
+                 rounding=rounding)
     s.init_moments(*state)
     s.step(warmup)
     torch.cuda.synchronize()
@@ -291,6 +295,48 @@ def precision_errors(prm, ref, got):
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     return {"mean_ux_profile": rel(prof(got[1]), prof(ref[1])), "u_field": rel(got[1], ref[1]),
             "pi_field": rel(got[2], ref[2])}
+
+
+def precision_study(T, torch, stream, prm, state, warm=1000, window=5000, every=250):
+    """The 16-bit storage study on the full channel: FP32, BF16 and FP16 runs from
+    the same initial state; the mean velocity U(y) and the Reynolds stresses
+    averaged over x, z and the samples of the last `window` of warm + window
+    steps, each 16-bit run compared with the FP32 run."""
+    from paper_2401_17074_b300 import workloads as W
+    from paper_2401_17074_b300.channel_stats import ChannelStats, profile_errors
+    dims = prm["dims"]
+    u = torch.empty((3, dims[0] * dims[1] * dims[2]), dtype=torch.float64, device="cuda")
+    runs = {}
+    for run in ("fp32", "bf16", "fp16", "bf16_sr", "fp16_sr"):
+        prec = run.split("_")[0]
+        s = T.Solver(dims, prm["tau"], force=prm["force"], bc=prm["bc"], precision=PREC_CODE[prec],
+                     stream=stream.cuda_stream, u_ref=0.05, pi_ref=W.pi_reference(state),
+                     rounding="stochastic" if run.endswith("_sr") else "nearest", rounding_seed=1)
+        s.init_moments(*state)
+        s.step(warm)
+        st = ChannelStats(dims)
+        for k in range(window // every + 1):
+            if k:
+                s.step(every)
+            T.tslb_get_moments(s.handle, None, u, None, T.DEVICE)
+            st.add(u)
+        _, code = s.diagnostics()
+        s.close()
+        runs[run] = (st.result(), code)
+    del u
+    torch.cuda.empty_cache()
+    ref = runs["fp32"][0]
+    out = {"workload": "channel %dx%dx%d from the bench's initial state, steps %d..%d, %d samples every %d steps"
+                       % (dims + (warm, warm + window, window // every + 1, every)),
+           "fp32_scale": {"U_max": float(ref["U"].max()), "uu_max": float(ref["uu"].max()),
+                          "vv_max": float(ref["vv"].max()), "ww_max": float(ref["ww"].max()),
+                          "uv_absmax": float(np.abs(ref["uv"]).max())},
+           "status": {k: v[1] for k, v in runs.items()}}
+    for run in ("bf16", "fp16", "bf16_sr", "fp16_sr"):
+        out[run + "_vs_fp32"] = profile_errors(runs[run][0], ref)
+    out["note"] = ("_sr: stochastic rounding of the stored rho - 1 and u; without it the per-step body-force "
+                   "increment (%.3g) is below half a 16-bit spacing of u and is lost" % prm["force"][0])
+    return out
 
 
 def time_jet_paper(T, torch, stream, steps=200, warmup=20):
@@ -472,6 +518,12 @@ def main():
             if fin is not None:
                 variants[prec]["error_vs_fp32_after_%d_steps" % (args.steps + args.warmup)] = \
                     precision_errors(prm, ref_final, fin)
+        msv, nv, dv, cv, _, _ = time_device(T, torch, prm, state, "bf16", kernel, args.steps, args.warmup, stream,
+                                            dist, rounding="stochastic")
+        variants["bf16_stochastic_rounding"] = {
+            "value": job_mlups(nv, ws, args.steps, msv), "unit": "MLUPS",
+            "roofline_frac": BYTES_PER_NODE["bf16"] * nv / (msv * 1e-3 / args.steps) / 1e9 / hbm,
+            "bytes_per_node": BYTES_PER_NODE["bf16"], "stable": cv == T.TSLB_OK}
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = time_e2e(T, torch, prm, state, args.steps, stream)
@@ -494,6 +546,9 @@ def main():
                      "ms_per_step": msn / k_nee, "status": cn},
                  "jet_paper": time_jet_paper(T, torch, stream),
                  "d2q9_channel": time_channel2d(T, torch, stream, hbm)}
+    study = None
+    if not args.no_precision_study and not args.no_variants and rank == 0:
+        study = precision_study(T, torch, stream, prm, state)
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(prm, args.cpu_seconds)
@@ -516,6 +571,7 @@ def main():
                          "algorithmic_bytes_per_node": bpn, "kernel": kname},
             "alu": alu,
             "variants": variants,
+            "precision_study": study,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,

@@ -95,6 +95,18 @@ typedef enum tslb_where { TSLB_HOST = 0, TSLB_DEVICE = 1 } tslb_where;
  * layer, and is not supported by tslb_adjoint_force_gradient. */
 typedef enum tslb_forcing { TSLB_FORCING_LUO = 0, TSLB_FORCING_GUO = 1 } tslb_forcing;
 
+/* Rounding of the 16-bit storage codecs when a step stores its moments.
+ * TSLB_ROUND_NEAREST rounds every stored value to nearest even.
+ * TSLB_ROUND_STOCHASTIC stores rho - 1 and u rounded up or down in magnitude with
+ * probabilities that make the stored value exact in expectation (16 random bits
+ * per value from a counter-based hash of (node, step, rounding_seed), so a run
+ * is reproducible and both step kernels draw the same bits); Pi^neq keeps
+ * rounding to nearest.  Rounding to nearest drops per-step increments below half
+ * a 16-bit spacing (a body force of 1e-7 on u ~ 0.05 in BF16), so a forced flow
+ * stops accelerating; stochastic rounding keeps them on average.  The initial
+ * state is always rounded to nearest.  Requires TSLB_BF16 or TSLB_FP16. */
+typedef enum tslb_rounding { TSLB_ROUND_NEAREST = 0, TSLB_ROUND_STOCHASTIC = 1 } tslb_rounding;
+
 typedef enum tslb_kernel {
     TSLB_KERNEL_AUTO = 0,     /* the fastest kernel that supports the configuration */
     TSLB_KERNEL_DIRECT = 1,   /* one thread per node, 27 direct gathers (cross-check path) */
@@ -142,6 +154,8 @@ typedef struct tslb_options {
     int sponge_width;
     double sponge_k;
     int forcing;          /* tslb_forcing, default TSLB_FORCING_LUO */
+    int rounding;         /* tslb_rounding, default TSLB_ROUND_NEAREST */
+    uint64_t rounding_seed; /* key of the stochastic rounding bits, default 0 */
 } tslb_options;
 
 typedef struct tslb_diag {

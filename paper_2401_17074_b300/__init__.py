@@ -29,6 +29,7 @@ HOST, DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED = 0, 1, 2
 TSLB_NOISE_UNIFORM, TSLB_NOISE_GAUSSIAN = 0, 1
 TSLB_FORCING_LUO, TSLB_FORCING_GUO = 0, 1
+TSLB_ROUND_NEAREST, TSLB_ROUND_STOCHASTIC = 0, 1
 
 EXPORTED = [
     "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_set_force_field", "tslb_step",
@@ -47,7 +48,8 @@ class tslb_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("u_ref", ctypes.c_double), ("pi_ref", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("checkpoint_every", ctypes.c_int), ("inflow", tslb_inflow), ("sponge_width", ctypes.c_int),
-                ("sponge_k", ctypes.c_double), ("forcing", ctypes.c_int)]
+                ("sponge_k", ctypes.c_double), ("forcing", ctypes.c_int), ("rounding", ctypes.c_int),
+                ("rounding_seed", ctypes.c_uint64)]
 
 
 class tslb_diag(ctypes.Structure):
@@ -234,9 +236,10 @@ class Solver:
 
     def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05, pi_ref=1e-3,
                  kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None, sponge=None,
-                 lattice=None, forcing="luo"):
+                 lattice=None, forcing="luo", rounding="nearest", rounding_seed=0):
         """inflow: dict(center2, diameter, u_jet, noise_amp, seed[, noise="uniform" | "gaussian"]);
-        sponge: (width, K) viscosity layer towards the z+ face (tslb_options.sponge_width / sponge_k)."""
+        sponge: (width, K) viscosity layer towards the z+ face (tslb_options.sponge_width / sponge_k);
+        rounding: "nearest" or "stochastic" (16-bit storage; tslb_options.rounding / rounding_seed)."""
         o = tslb_options_default()
         o.precision = int(precision)
         o.u_ref = float(u_ref)
@@ -256,6 +259,8 @@ class Solver:
             o.inflow.noise_kind = {"uniform": TSLB_NOISE_UNIFORM,
                                    "gaussian": TSLB_NOISE_GAUSSIAN}[inflow.get("noise", "uniform")]
         o.forcing = {"luo": TSLB_FORCING_LUO, "guo": TSLB_FORCING_GUO}[forcing]
+        o.rounding = {"nearest": TSLB_ROUND_NEAREST, "stochastic": TSLB_ROUND_STOCHASTIC}[rounding]
+        o.rounding_seed = int(rounding_seed)
         if sponge is not None:
             o.sponge_width = int(sponge[0])
             o.sponge_k = float(sponge[1])

@@ -280,6 +280,7 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
         for (int64_t j = 0; j < len && e == cudaSuccess; ++j) {
             Physics pj = p;
             pj.t = n_beg + j;
+            pj.sr_key = sr_step_key(h->rounding_seed, pj.t);
             e = launch_step_any(h, seg + j * state_bytes, seg + (j + 1) * state_bytes, pj);
         }
         for (int64_t n = n_end - 1; n >= n_beg && e == cudaSuccess; --n) {

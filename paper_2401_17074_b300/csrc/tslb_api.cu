@@ -112,6 +112,7 @@ Physics make_physics(const tslb_s* h) {
         p.inv_s_u = (float)(1.0 / h->u_ref);
         p.inv_s_pi = (float)(1.0 / h->pi_ref);
     }
+    p.sr_key = sr_step_key(h->rounding_seed, h->t);
     p.omega1_pi = (float)((1.0 - h->omega) * (double)p.s_pi);
     p.pi_store = (float)((double)p.inv_s_pi / 216.0);
     return p;
@@ -202,6 +203,10 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "D2Q9: periodic x, periodic or bounce-back y");
     if (o.forcing != TSLB_FORCING_LUO && o.forcing != TSLB_FORCING_GUO)
         return fail(nullptr, TSLB_ERR_INVALID, "unknown forcing scheme");
+    if (o.rounding != TSLB_ROUND_NEAREST && o.rounding != TSLB_ROUND_STOCHASTIC)
+        return fail(nullptr, TSLB_ERR_INVALID, "unknown rounding mode");
+    if (o.rounding == TSLB_ROUND_STOCHASTIC && o.precision == TSLB_FP32)
+        return fail(nullptr, TSLB_ERR_INVALID, "stochastic rounding applies to 16-bit storage");
     if (o.forcing == TSLB_FORCING_GUO &&
         (d2 || bx != TSLB_BC_PERIODIC || bz0 != TSLB_BC_PERIODIC || by == TSLB_BC_NEE_WALL || o.sponge_width != 0))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED,
@@ -235,6 +240,8 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     h->inflow = o.inflow;
     h->sponge_width = o.sponge_width;
     h->forcing = o.forcing;
+    h->rounding = o.rounding;
+    h->rounding_seed = o.rounding_seed;
     h->sponge_k = o.sponge_k;
     h->elem = o.precision == TSLB_FP32 ? 4 : 2;
 

@@ -76,9 +76,29 @@ struct Physics {
     // (1 - omega) * s_pi, applied to Pi decoded without its storage scale, and
     // inv_s_pi / 216, the factor from the 216-scaled sums to stored Pi
     float omega1_pi, pi_store;
+    // key of this step's stochastic-rounding bits (sr_step_key of the seed and
+    // t); read by the stochastic-rounding codecs only
+    uint32_t sr_key;
     // sponge layer: (1 - omega) per full-lattice z, or nullptr (uniform omega)
     const float* omega1_z;
 };
+
+// ---- stochastic rounding ------------------------------------------------------
+// Integer hash with low bias: two xorshift-multiply rounds (C. Wellons,
+// "Prospecting for hash functions", 2018, the lowbias32 construction).
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+// Key of the random bits used when storing the state at t + 1 (the step that
+// reads the state at t); nodes draw mix32(node ^ key) and a second word from it.
+__host__ __device__ __forceinline__ uint32_t sr_step_key(unsigned long long seed, long long t) {
+    return mix32((uint32_t)seed ^ mix32((uint32_t)t ^ mix32((uint32_t)(seed >> 32) ^ 0x5bd1e995U)));
+}
 
 // ---- storage ----------------------------------------------------------------
 // One moment buffer holds three arrays of small vectors, one entry per stored
@@ -89,21 +109,59 @@ struct Physics {
 // (fs = node count padded to 128; 10 * fs elements per buffer).  FP32 storage
 // moves 16 + 16 + 8 bytes per node, 16-bit storage 8 + 8 + 4, each warp access
 // contiguous.  The 16-bit codecs store u / u_ref and Pi / pi_ref (rho - 1
-// unscaled), rounded to nearest even.
+// unscaled), rounded to nearest even, or -- with stochastic rounding -- u and
+// rho - 1 rounded up or down in magnitude with probabilities that make the
+// stored value exact in expectation (16 random bits per value).  Those two are
+// the conserved moments: each step adds to them increments (a body force of
+// 1e-7 per step, say) far below half a 16-bit spacing, which rounding to
+// nearest would drop every step.  Pi^neq is rebuilt from the gathered
+// populations every step and keeps rounding to nearest.
 struct CodecF32 {
     typedef float T;
+    static constexpr bool SR = false;
 };
 struct CodecBF16 {
+    static constexpr bool SR = false;
     typedef __nv_bfloat16 T;
     typedef __nv_bfloat162 T2;
     static __device__ __forceinline__ float2 to_f2(T2 v) { return __bfloat1622float2(v); }
     static __device__ __forceinline__ T2 from_f2(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    // Stochastic rounding to BF16 (the upper half of the FP32 pattern): add 16
+    // random bits below the kept ones and truncate, which carries into the kept
+    // bits with probability (dropped part) / (BF16 spacing), in magnitude.  NaN
+    // is kept as it is (adding to its payload could carry into the sign).
+    static __device__ __forceinline__ unsigned pack_sr(float a, float b, uint32_t r) {
+        const uint32_t ba = __float_as_uint(a), bb = __float_as_uint(b);
+        const uint32_t ua = a != a ? ba : ba + (r & 0xffffu);
+        const uint32_t ub = b != b ? bb : bb + (r >> 16);
+        return __byte_perm(ua, ub, 0x7632);
+    }
 };
 struct CodecF16 {
+    static constexpr bool SR = false;
     typedef __half T;
     typedef __half2 T2;
     static __device__ __forceinline__ float2 to_f2(T2 v) { return __half22float2(v); }
     static __device__ __forceinline__ T2 from_f2(float a, float b) { return __floats2half2_rn(a, b); }
+    // Stochastic rounding to FP16: add U * (FP16 spacing at |x|) in the
+    // direction of x, U = r16 / 2^16, and convert toward zero.  The spacing is
+    // 2^(e - 10) for |x| in [2^e, 2^(e+1)), and 2^-24 below the normal range.
+    static __device__ __forceinline__ __half sr1(float x, uint32_t r16) {
+        const int e = max((int)((__float_as_uint(x) >> 23) & 0xffu) - 127, -14);
+        const float ulp = __uint_as_float((uint32_t)(e + 117) << 23);
+        return __float2half_rz(fmaf(copysignf((float)r16 * (1.0f / 65536.0f), x), ulp, x));
+    }
+    static __device__ __forceinline__ unsigned pack_sr(float a, float b, uint32_t r) {
+        const __half2 v = __halves2half2(sr1(a, r & 0xffffu), sr1(b, r >> 16));
+        return *reinterpret_cast<const unsigned*>(&v);
+    }
+};
+// The same storage formats with stochastic rounding of rho - 1 and u in the step.
+struct CodecBF16SR : CodecBF16 {
+    static constexpr bool SR = true;
+};
+struct CodecF16SR : CodecF16 {
+    static constexpr bool SR = true;
 };
 
 template <class Codec>
@@ -182,18 +240,28 @@ struct NodeIO {
         m[F_PXZ] = t.x;
         m[F_PYZ] = t.y;
     }
+    // V0 = (u_x, u_y, u_z, rho - 1) in storage units, rounded to nearest or
+    // stochastically (random words drawn from the node index and the step key).
+    static __device__ __forceinline__ uint2 v0_word(long long n, const Physics& p, const float m[NFIELDS]) {
+        const float iu = p.inv_s_u;
+        if (Codec::SR) {
+            const uint32_t w0 = mix32((uint32_t)n ^ p.sr_key), w1 = mix32(w0 ^ 0x9e3779b9U);
+            return make_uint2(Codec::pack_sr(m[F_UX] * iu, m[F_UY] * iu, w0),
+                              Codec::pack_sr(m[F_UZ] * iu, m[F_DRHO], w1));
+        }
+        return make_uint2(pack(m[F_UX] * iu, m[F_UY] * iu), pack(m[F_UZ] * iu, m[F_DRHO]));
+    }
     // Same as store with Pi already in storage units.
     static __device__ __forceinline__ void store_rawpi(T* __restrict__ b, long long fs, long long n, const Physics& p,
                                                        const float m[NFIELDS]) {
-        const float iu = p.inv_s_u;
-        reinterpret_cast<uint2*>(b)[n] = make_uint2(pack(m[F_UX] * iu, m[F_UY] * iu), pack(m[F_UZ] * iu, m[F_DRHO]));
+        reinterpret_cast<uint2*>(b)[n] = v0_word(n, p, m);
         reinterpret_cast<uint2*>(b + 4 * fs)[n] = make_uint2(pack(m[F_PXX], m[F_PYY]), pack(m[F_PZZ], m[F_PXY]));
         reinterpret_cast<unsigned*>(b + 8 * fs)[n] = pack(m[F_PXZ], m[F_PYZ]);
     }
     static __device__ __forceinline__ void store(T* __restrict__ b, long long fs, long long n, const Physics& p,
                                                  const float m[NFIELDS]) {
-        const float iu = p.inv_s_u, ip = p.inv_s_pi;
-        reinterpret_cast<uint2*>(b)[n] = make_uint2(pack(m[F_UX] * iu, m[F_UY] * iu), pack(m[F_UZ] * iu, m[F_DRHO]));
+        const float ip = p.inv_s_pi;
+        reinterpret_cast<uint2*>(b)[n] = v0_word(n, p, m);
         reinterpret_cast<uint2*>(b + 4 * fs)[n] =
             make_uint2(pack(m[F_PXX] * ip, m[F_PYY] * ip), pack(m[F_PZZ] * ip, m[F_PXY] * ip));
         reinterpret_cast<unsigned*>(b + 8 * fs)[n] = pack(m[F_PXZ] * ip, m[F_PYZ] * ip);
@@ -445,6 +513,8 @@ struct tslb_s {
     double sponge_k = 0.0;
     float* omega1_z = nullptr;  // sponge layer table, (1 - omega) per full-lattice z
     int forcing = TSLB_FORCING_LUO;
+    int rounding = TSLB_ROUND_NEAREST;
+    unsigned long long rounding_seed = 0;
     size_t elem = 4;
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;

@@ -144,12 +144,20 @@ cudaError_t launch_step_direct(const tslb_s* h, const void* src, void* dst, cons
             step_direct_kernel<CodecF32><<<blocks, threads, 0, h->stream>>>((const float*)src, (float*)dst, h->g, p);
             break;
         case TSLB_BF16:
-            step_direct_kernel<CodecBF16><<<blocks, threads, 0, h->stream>>>(
-                (const __nv_bfloat16*)src, (__nv_bfloat16*)dst, h->g, p);
+            if (h->rounding == TSLB_ROUND_STOCHASTIC)
+                step_direct_kernel<CodecBF16SR><<<blocks, threads, 0, h->stream>>>(
+                    (const __nv_bfloat16*)src, (__nv_bfloat16*)dst, h->g, p);
+            else
+                step_direct_kernel<CodecBF16><<<blocks, threads, 0, h->stream>>>(
+                    (const __nv_bfloat16*)src, (__nv_bfloat16*)dst, h->g, p);
             break;
         default:
-            step_direct_kernel<CodecF16><<<blocks, threads, 0, h->stream>>>((const __half*)src, (__half*)dst, h->g,
-                                                                            p);
+            if (h->rounding == TSLB_ROUND_STOCHASTIC)
+                step_direct_kernel<CodecF16SR><<<blocks, threads, 0, h->stream>>>((const __half*)src, (__half*)dst,
+                                                                                  h->g, p);
+            else
+                step_direct_kernel<CodecF16><<<blocks, threads, 0, h->stream>>>((const __half*)src, (__half*)dst,
+                                                                                h->g, p);
             break;
     }
     return cudaGetLastError();

@@ -729,8 +729,12 @@ bool factored_supports(const tslb_s* h) {
 cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p) {
     switch (h->precision) {
         case TSLB_FP32: return launch_codec<CodecF32>(h, src, dst, p);
-        case TSLB_BF16: return launch_codec<CodecBF16>(h, src, dst, p);
-        default: return launch_codec<CodecF16>(h, src, dst, p);
+        case TSLB_BF16:
+            return h->rounding == TSLB_ROUND_STOCHASTIC ? launch_codec<CodecBF16SR>(h, src, dst, p)
+                                                        : launch_codec<CodecBF16>(h, src, dst, p);
+        default:
+            return h->rounding == TSLB_ROUND_STOCHASTIC ? launch_codec<CodecF16SR>(h, src, dst, p)
+                                                        : launch_codec<CodecF16>(h, src, dst, p);
     }
 }
 

@@ -94,6 +94,16 @@ def test_bad_option_values_rejected():
     assert c == T.TSLB_ERR_INVALID
 
 
+def test_rounding_rules():
+    o = T.tslb_options_default()
+    assert o.rounding == T.TSLB_ROUND_NEAREST and o.rounding_seed == 0
+    o.rounding = 5
+    assert _create_code(opt=o)[0] == T.TSLB_ERR_INVALID
+    o = T.tslb_options_default()
+    o.rounding = T.TSLB_ROUND_STOCHASTIC  # FP32 storage has nothing to round
+    assert _create_code(opt=o)[0] == T.TSLB_ERR_INVALID
+
+
 def test_bad_sponge_and_noise_rejected():
     for width, k in ((-1, 10.0), (8, 10.0), (3, -1.0), (3, float("nan"))):  # dims z = 8
         o = T.tslb_options_default()

@@ -71,3 +71,37 @@ def test_channel_mean_profile(cuda_ok, prec):
     err = _rel(prof(ug), prof(uo))
     bound = 1e-5 if prec == T.FP32 else 4 * EPS[prec]
     assert err <= bound, err
+
+
+def test_channel_statistics_against_oracle(cuda_ok):
+    """Mean velocity and Reynolds-stress profiles of the forced channel,
+    averaged over x, z and the samples at steps 10, 20 and 30 (FP32 storage),
+    against the same statistics of the oracle run.
+
+    Bounds: U(y) inherits the 1e-5 relative bound of u_x over these steps (the
+    small forced-channel parity test).  A stress <u'_i u'_j> changes by about
+    2 <u' du> for a field error du, so its relative error is at most about
+    2 |du| / |u'|; with |du| <= 1e-5 |u| and fluctuations of 2 % of the
+    centreline velocity (the initial noise) that is 1e-3.
+    """
+    from paper_2401_17074_b300.channel_stats import ChannelStats, profile_errors
+    prm = W.channel_params(nx=20, ny=18, nz=12, u_tau=0.0035, tau=0.503)
+    state = W.channel_state(prm, seed=1)
+    dims = prm["dims"]
+    o = oracle.OracleSim(dims, prm["tau"], force=prm["force"], bc=prm["bc"])
+    o.init_moments(*state)
+    s = T.Solver(dims, prm["tau"], force=prm["force"], bc=prm["bc"])
+    s.init_moments(*state)
+    so, sg = ChannelStats(dims), ChannelStats(dims)
+    for _ in range(3):
+        o.step(10)
+        s.step(10)
+        so.add(o.get_moments()[1])
+        sg.add(s.get_moments()[1])
+    s.close()
+    ref, got = so.result(), sg.result()
+    assert min(np.abs(ref["uu"]).max(), ref["vv"].max(), ref["ww"].max()) > 0.0
+    errs = profile_errors(got, ref)
+    assert errs["U"] <= 1e-5, errs
+    for k in ("uu", "vv", "ww", "uv"):
+        assert errs[k] <= 1e-3, errs
