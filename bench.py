@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workload lines")
     ap.add_argument("--no-precision-study", action="store_true",
                     help="skip the time-averaged FP32 / BF16 / FP16 channel statistics")
-    ap.add_argument("--only", default=None, choices=["d2q9"], help="time one extra workload alone (profiling)")
+    ap.add_argument("--only", default=None, choices=["d2q9", "adjoint"],
+                    help="time one extra workload alone (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -479,6 +480,11 @@ def main():
         torch.cuda.set_device(0)
     import paper_2401_17074_b300 as T
     T.load()
+    if args.only == "adjoint":
+        line = time_adjoint(T, torch, torch.cuda.Stream())
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     if args.only == "d2q9":
         hbm, hbm_src = measured_peaks()
         line = time_channel2d(T, torch, torch.cuda.Stream(), hbm, steps=args.steps, warmup=args.warmup)

@@ -211,7 +211,10 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out);
  * `nsteps` steps taken since tslb_init_moments by the discrete adjoint of the
  * step.  Requires options.checkpoint_every > 0 at create time; segments
  * between checkpoints are recomputed.  dJdF is a full-lattice FP32 [3][N]
- * array (boundary entries 0).  Synchronises the stream. */
+ * array (boundary entries 0).  Synchronises the stream.  The first call
+ * allocates a workspace of checkpoint_every moment states plus 23 FP32 values
+ * per node, which the handle keeps for later calls until tslb_destroy.
+ * Periodic boxes of fewer than 2^31 nodes, Luo forcing, no sponge layer. */
 int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where);
 
 /* ---- Diagnostics without allocation ------------------------------------

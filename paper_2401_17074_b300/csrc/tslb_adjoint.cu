@@ -5,9 +5,12 @@
 //   G(x)  = sum_i T_i A(x - c_i)        linear gather (streaming, Eq. pushLB, and moment sums)
 //   m'(x) = finish(G(x))                local, nonlinear (rho, u, Pi^neq from the sums)
 // so the adjoint of one step is
-//   Gbar(x) = (d finish / d G)^T lambda'(x)           (kernel adj_finish)
-//   Abar(y) = sum_i T_i^T Gbar(y + c_i)                (transpose gather, kernel adj_gather)
+//   Gbar(x) = (d finish / d G)^T lambda'(x)
+//   Abar(y) = sum_i T_i^T Gbar(y + c_i)                (transpose gather)
 //   lambda(y) = (d modes / d m)^T Abar(y),  Fbar(y) += (d modes / d F)^T Abar(y).
+// lambda(y) and the state m(y) it pairs with are all the next (earlier) step's
+// first map needs, so kernel adj_gather ends with that step's Gbar(y) and the
+// lambda array is never stored; adj_seed does the same for the final step.
 // The objective is J = 1/2 sum rho |u|^2 at the final step; the control is a
 // time-constant per-node acceleration field.  Segments between the forward
 // checkpoints are recomputed with the forward kernel (bitwise identical
@@ -25,41 +28,18 @@ __device__ __forceinline__ void load_m(const typename Codec::T* __restrict__ src
     NodeIO<Codec>::load(src, fs, idx, p, m);
 }
 
-// lambda at the final step: dJ/d(rho-1) = |u|^2 / 2, dJ/du = rho u, dJ/dPi = 0.
-template <class Codec>
-__global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __restrict__ lam, Geometry g, Physics p) {
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= g.plane * g.nz) return;
-    float m[NFIELDS];
-    load_m<Codec>(m_end, g.fstride, n, p, m);
-    const float rho = 1.0f + m[F_DRHO];
-    lam[F_DRHO * g.fstride + n] = 0.5f * (m[F_UX] * m[F_UX] + m[F_UY] * m[F_UY] + m[F_UZ] * m[F_UZ]);
-    lam[F_UX * g.fstride + n] = rho * m[F_UX];
-    lam[F_UY * g.fstride + n] = rho * m[F_UY];
-    lam[F_UZ * g.fstride + n] = rho * m[F_UZ];
-    for (int k = 0; k < 6; ++k) lam[(F_PXX + k) * g.fstride + n] = 0.0f;
-}
-
-// Transpose of finish_moments: G = (D0, J, S) -> (drho', u', Pi') with
+// Transpose of finish_moments at one node: G = (D0, J, S) -> (drho', u', Pi') with
 //   drho' = D0/216, u_a = J_a / r (r = 216 + D0),
-//   Pi_aa = (S_aa - J_a^2 / r - D0/3)/216, Pi_ab = (S_ab - J_a J_b / r)/216.
-// Gbar layout: [D0, Jx, Jy, Jz, Sxx, Syy, Szz, Sxy, Sxz, Syz].
-template <class Codec>
-__global__ void adj_finish(const float* __restrict__ lam, const typename Codec::T* __restrict__ m_next,
-                           float* __restrict__ gbar, Geometry g, Physics p) {
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= g.plane * g.nz) return;
-    float m[NFIELDS], l[NFIELDS];
-    load_m<Codec>(m_next, g.fstride, n, p, m);
-#pragma unroll
-    for (int f = 0; f < NFIELDS; ++f) l[f] = lam[f * g.fstride + n];
+//   Pi_aa = (S_aa - J_a^2 / r - D0/3)/216, Pi_ab = (S_ab - J_a J_b / r)/216,
+// evaluated at the state m that finish produced.  gb layout: [D0, Jx, Jy, Jz,
+// Sxx, Syy, Szz, Sxy, Sxz, Syz].
+__device__ __forceinline__ void finish_transpose(const float m[NFIELDS], const float l[NFIELDS], float gb[NFIELDS]) {
     const float u[3] = {m[F_UX], m[F_UY], m[F_UZ]};
     const float inv_r = 1.0f / (216.0f * (1.0f + m[F_DRHO]));
     const float k = 1.0f / 216.0f;
     // lambda_Pi as a symmetric matrix
     const float L[3][3] = {{l[F_PXX], l[F_PXY], l[F_PXZ]}, {l[F_PXY], l[F_PYY], l[F_PYZ]}, {l[F_PXZ], l[F_PYZ], l[F_PZZ]}};
     float gD = l[F_DRHO] * k;
-    float gJ[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         gD -= u[a] * l[F_UX + a] * inv_r;
@@ -68,51 +48,86 @@ __global__ void adj_finish(const float* __restrict__ lam, const typename Codec::
 #pragma unroll
         for (int b = 0; b < 3; ++b)
             if (b != a) s += u[b] * L[a][b];
-        gJ[a] = l[F_UX + a] * inv_r - s * k;
+        gb[1 + a] = l[F_UX + a] * inv_r - s * k;
     }
     gD += (u[0] * u[1] * L[0][1] + u[0] * u[2] * L[0][2] + u[1] * u[2] * L[1][2]) * k;
-    gbar[0 * g.fstride + n] = gD;
-    gbar[1 * g.fstride + n] = gJ[0];
-    gbar[2 * g.fstride + n] = gJ[1];
-    gbar[3 * g.fstride + n] = gJ[2];
-    for (int c = 0; c < 6; ++c) gbar[(4 + c) * g.fstride + n] = l[F_PXX + c] * k;
+    gb[0] = gD;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) gb[4 + c] = l[F_PXX + c] * k;
 }
 
-// Transpose gather + transpose of post_modes at the source node y.
+// Final step: lambda = dJ/dm with dJ/d(rho-1) = |u|^2 / 2, dJ/du = rho u,
+// dJ/dPi = 0, and the Gbar of the last forward step from it.
 template <class Codec>
-__global__ void __launch_bounds__(256) adj_gather(const float* __restrict__ gbar, const typename Codec::T* __restrict__ m_cur,
-                                                  float* __restrict__ lam, float* __restrict__ fbar, Geometry g,
+__global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __restrict__ gbar, Geometry g, Physics p) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.plane * g.nz) return;
+    float m[NFIELDS], l[NFIELDS], gb[NFIELDS];
+    load_m<Codec>(m_end, g.fstride, n, p, m);
+    const float rho = 1.0f + m[F_DRHO];
+    l[F_DRHO] = 0.5f * (m[F_UX] * m[F_UX] + m[F_UY] * m[F_UY] + m[F_UZ] * m[F_UZ]);
+    l[F_UX] = rho * m[F_UX];
+    l[F_UY] = rho * m[F_UY];
+    l[F_UZ] = rho * m[F_UZ];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) l[F_PXX + k] = 0.0f;
+    finish_transpose(m, l, gb);
+#pragma unroll
+    for (int f = 0; f < NFIELDS; ++f) gbar[f * g.fstride + n] = gb[f];
+}
+
+// Transpose gather + transpose of post_modes at the source node y, then the
+// Gbar of the preceding step at y (gbar_in belongs to the step m_cur -> m_next,
+// gbar_out to the step before it).
+// The 27 directions are unrolled, so every coefficient below is a constant:
+// a direction loads only the moment sums whose monomial psi_t(c) is nonzero
+// (1, 3, 6 or 10 of them for c with 0, 1, 2 or 3 nonzero components), and
+// adds only to the modes whose weight w(c) phi_k(c) is nonzero (phi_1(0) = 0).
+template <class Codec>
+__global__ void __launch_bounds__(256) adj_gather(const float* __restrict__ gbar,
+                                                  const typename Codec::T* __restrict__ m_cur,
+                                                  float* __restrict__ gbar_out, float* __restrict__ fbar, Geometry g,
                                                   Physics p) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.plane * g.nz) return;
     const int y0 = (int)(n % g.nx), y1 = (int)((n / g.nx) % g.ny), y2 = (int)(n / g.plane);
+    // neighbour offsets per axis (periodic), index c + 1
+    const unsigned X[3] = {(unsigned)(y0 == 0 ? g.nx - 1 : y0 - 1), (unsigned)y0,
+                           (unsigned)(y0 == g.nx - 1 ? 0 : y0 + 1)};
+    const unsigned nx = (unsigned)g.nx, pl = (unsigned)g.plane;
+    const unsigned Y[3] = {nx * (unsigned)(y1 == 0 ? g.ny - 1 : y1 - 1), nx * (unsigned)y1,
+                           nx * (unsigned)(y1 == g.ny - 1 ? 0 : y1 + 1)};
+    const unsigned Z[3] = {pl * (unsigned)(y2 == 0 ? g.nz - 1 : y2 - 1), pl * (unsigned)y2,
+                           pl * (unsigned)(y2 == g.nz - 1 ? 0 : y2 + 1)};
+    const long long fs = g.fstride;
     float Ab[NMODES];
 #pragma unroll
     for (int k = 0; k < NMODES; ++k) Ab[k] = 0.0f;
+#pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
+#pragma unroll
         for (int cy = -1; cy <= 1; ++cy)
+#pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
-                const int x0 = (y0 + cx + g.nx) % g.nx, x1 = (y1 + cy + g.ny) % g.ny, x2 = (y2 + cz + g.nz) % g.nz;
-                const long long xi = (long long)x0 + (long long)g.nx * x1 + g.plane * x2;
-                const float* G = gbar + xi;
-                const long long fs = g.fstride;
-                // adjoint population: psi(c) . Gbar(y + c)
-                float gb = G[0];
-                gb = fmaf((float)cx, G[1 * fs], gb);
-                gb = fmaf((float)cy, G[2 * fs], gb);
-                gb = fmaf((float)cz, G[3 * fs], gb);
-                gb = fmaf((float)(cx * cx), G[4 * fs], gb);
-                gb = fmaf((float)(cy * cy), G[5 * fs], gb);
-                gb = fmaf((float)(cz * cz), G[6 * fs], gb);
-                gb = fmaf((float)(cx * cy), G[7 * fs], gb);
-                gb = fmaf((float)(cx * cz), G[8 * fs], gb);
-                gb = fmaf((float)(cy * cz), G[9 * fs], gb);
-                gb *= wgt(cx) * wgt(cy) * wgt(cz);
+                const float* G = gbar + (X[cx + 1] + Y[cy + 1] + Z[cz + 1]);
+                // adjoint population: psi(c) . Gbar(y + c), nonzero terms only
+                float gb = __ldg(G);
+                if (cx != 0) gb = fmaf((float)cx, __ldg(G + 1 * fs), gb);
+                if (cy != 0) gb = fmaf((float)cy, __ldg(G + 2 * fs), gb);
+                if (cz != 0) gb = fmaf((float)cz, __ldg(G + 3 * fs), gb);
+                if (cx != 0) gb += __ldg(G + 4 * fs);
+                if (cy != 0) gb += __ldg(G + 5 * fs);
+                if (cz != 0) gb += __ldg(G + 6 * fs);
+                if (cx != 0 && cy != 0) gb = fmaf((float)(cx * cy), __ldg(G + 7 * fs), gb);
+                if (cx != 0 && cz != 0) gb = fmaf((float)(cx * cz), __ldg(G + 8 * fs), gb);
+                if (cy != 0 && cz != 0) gb = fmaf((float)(cy * cz), __ldg(G + 9 * fs), gb);
+                const float w = wgt(cx) * wgt(cy) * wgt(cz);
 #pragma unroll
                 for (int k = 0; k < NMODES; ++k) {
                     int k1, k2, k3;
                     mode_digits(k, k1, k2, k3);
-                    Ab[k] = fmaf(gb, phi(k1, cx) * phi(k2, cy) * phi(k3, cz), Ab[k]);
+                    const float c = w * phi(k1, cx) * phi(k2, cy) * phi(k3, cz);
+                    if (c != 0.0f) Ab[k] = fmaf(c, gb, Ab[k]);
                 }
             }
     // transpose of post_modes (u = v, constant or per-node force)
@@ -188,17 +203,21 @@ __global__ void __launch_bounds__(256) adj_gather(const float* __restrict__ gbar
         lP[0][2] += w1 * u[1] * ab;
         lP[0][1] += w1 * u[2] * ab;
     }
-    const long long fs = g.fstride;
-    lam[F_DRHO * fs + n] = lr;
-    lam[F_UX * fs + n] = lu[0];
-    lam[F_UY * fs + n] = lu[1];
-    lam[F_UZ * fs + n] = lu[2];
-    lam[F_PXX * fs + n] = lP[0][0];
-    lam[F_PYY * fs + n] = lP[1][1];
-    lam[F_PZZ * fs + n] = lP[2][2];
-    lam[F_PXY * fs + n] = lP[0][1];
-    lam[F_PXZ * fs + n] = lP[0][2];
-    lam[F_PYZ * fs + n] = lP[1][2];
+    float l[NFIELDS];
+    l[F_DRHO] = lr;
+    l[F_UX] = lu[0];
+    l[F_UY] = lu[1];
+    l[F_UZ] = lu[2];
+    l[F_PXX] = lP[0][0];
+    l[F_PYY] = lP[1][1];
+    l[F_PZZ] = lP[2][2];
+    l[F_PXY] = lP[0][1];
+    l[F_PXZ] = lP[0][2];
+    l[F_PYZ] = lP[1][2];
+    float gb[NFIELDS];
+    finish_transpose(m, l, gb);
+#pragma unroll
+    for (int f = 0; f < NFIELDS; ++f) gbar_out[f * fs + n] = gb[f];
     fbar[n] += fb[0];
     fbar[fs + n] += fb[1];
     fbar[2 * fs + n] += fb[2];
@@ -211,7 +230,6 @@ cudaError_t adj_launch_all(const tslb_s* h, int which, const void* a, const void
     const unsigned blocks = (unsigned)((total + 255) / 256);
     typedef typename Codec::T T;
     if (which == 0) adj_seed<Codec><<<blocks, 256, 0, h->stream>>>((const T*)a, c, h->g, p);
-    else if (which == 1) adj_finish<Codec><<<blocks, 256, 0, h->stream>>>((const float*)b, (const T*)a, c, h->g, p);
     else adj_gather<Codec><<<blocks, 256, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
     return cudaGetLastError();
 }
@@ -239,6 +257,10 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
         *msg = "create the handle with options.checkpoint_every > 0";
         return TSLB_ERR_STATE;
     }
+    if (g.plane * g.nz >= (1LL << 31)) {
+        *msg = "the adjoint supports up to 2^31 - 1 nodes";
+        return TSLB_ERR_UNSUPPORTED;
+    }
     if (nsteps <= 0 || nsteps > h->t || (h->t - nsteps) % k != 0) {
         *msg = "nsteps must be in (0, steps taken] with (steps taken - nsteps) a multiple of checkpoint_every";
         return TSLB_ERR_INVALID;
@@ -249,27 +271,34 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
     }
     const size_t fs = (size_t)g.fstride;
     const size_t state_bytes = (size_t)NFIELDS * fs * h->elem;
-    float *lam = nullptr, *gbar = nullptr, *fbar = nullptr;
-    char* seg = nullptr;
-    cudaError_t e = cudaMalloc(&lam, sizeof(float) * NFIELDS * fs);
-    if (e == cudaSuccess) e = cudaMalloc(&gbar, sizeof(float) * NFIELDS * fs);
-    if (e == cudaSuccess) e = cudaMalloc(&fbar, sizeof(float) * 3 * fs);
-    if (e == cudaSuccess) e = cudaMalloc(&seg, state_bytes * (size_t)(k + 1));
-    auto cleanup = [&]() {
+    // workspace, kept in the handle across calls: Gbar of the current step and
+    // of the one before, the force gradient, and one recomputed segment (every
+    // part a multiple of 512 bytes: fs is padded to 128 nodes)
+    const size_t gbar_bytes = sizeof(float) * NFIELDS * fs, fbar_bytes = sizeof(float) * 3 * fs;
+    const size_t need = 2 * gbar_bytes + fbar_bytes + state_bytes * (size_t)k;
+    cudaError_t e = cudaSuccess;
+    if (h->adj_ws_bytes < need) {
         cudaStreamSynchronize(h->stream);
-        cudaFree(lam);
-        cudaFree(gbar);
-        cudaFree(fbar);
-        cudaFree(seg);
-    };
-    if (e != cudaSuccess) {
-        cleanup();
-        *msg = "adjoint workspace allocation failed";
-        return TSLB_ERR_ALLOC;
+        if (h->adj_ws) cudaFree(h->adj_ws);
+        h->adj_ws = nullptr;
+        h->adj_ws_bytes = 0;
+        e = cudaMalloc(&h->adj_ws, need);
+        if (e != cudaSuccess) {
+            h->adj_ws = nullptr;
+            *msg = "adjoint workspace allocation failed";
+            return TSLB_ERR_ALLOC;
+        }
+        h->adj_ws_bytes = need;
     }
+    char* ws = static_cast<char*>(h->adj_ws);
+    float* gbar[2] = {reinterpret_cast<float*>(ws), reinterpret_cast<float*>(ws + gbar_bytes)};
+    float* fbar = reinterpret_cast<float*>(ws + 2 * gbar_bytes);
+    char* seg = ws + 2 * gbar_bytes + fbar_bytes;
+    auto cleanup = [&]() { cudaStreamSynchronize(h->stream); };
     Physics p = make_physics(h);
     e = cudaMemsetAsync(fbar, 0, sizeof(float) * 3 * fs, h->stream);
-    if (e == cudaSuccess) e = adj_launch(h, 0, h->buf[h->cur], nullptr, lam, nullptr, p);
+    int cur = 0;
+    if (e == cudaSuccess) e = adj_launch(h, 0, h->buf[h->cur], nullptr, gbar[cur], nullptr, p);
     int64_t n_end = h->t;
     const int64_t n_stop = h->t - nsteps;
     while (e == cudaSuccess && n_end > n_stop) {
@@ -277,17 +306,17 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
         const int64_t n_beg = s * k;
         const int64_t len = n_end - n_beg;
         e = cudaMemcpyAsync(seg, h->ckpts[s], state_bytes, cudaMemcpyDeviceToDevice, h->stream);
-        for (int64_t j = 0; j < len && e == cudaSuccess; ++j) {
+        // states n_beg .. n_end - 1 (the gather of step n needs m(n) only)
+        for (int64_t j = 0; j + 1 < len && e == cudaSuccess; ++j) {
             Physics pj = p;
             pj.t = n_beg + j;
             pj.sr_key = sr_step_key(h->rounding_seed, pj.t);
             e = launch_step_any(h, seg + j * state_bytes, seg + (j + 1) * state_bytes, pj);
         }
         for (int64_t n = n_end - 1; n >= n_beg && e == cudaSuccess; --n) {
-            const char* m_next = seg + (n + 1 - n_beg) * state_bytes;
             const char* m_cur = seg + (n - n_beg) * state_bytes;
-            e = adj_launch(h, 1, m_next, lam, gbar, nullptr, p);
-            if (e == cudaSuccess) e = adj_launch(h, 2, m_cur, gbar, lam, fbar, p);
+            e = adj_launch(h, 1, m_cur, gbar[cur], gbar[cur ^ 1], fbar, p);
+            cur ^= 1;
         }
         n_end = n_beg;
     }

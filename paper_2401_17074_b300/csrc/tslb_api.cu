@@ -77,6 +77,7 @@ void release(tslb_s* h) {
     if (h->omega1_z) cudaFree(h->omega1_z);
     if (h->diag_host) cudaFreeHost(h->diag_host);
     for (void* c : h->ckpts) cudaFree(c);
+    if (h->adj_ws) cudaFree(h->adj_ws);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

@@ -526,6 +526,11 @@ struct tslb_s {
     double* diag_host = nullptr;
     // adjoint checkpoints: ckpts[s] holds the moments at step s * checkpoint_every
     std::vector<void*> ckpts;
+    // adjoint workspace (two Gbar arrays, the force gradient, one recomputed
+    // segment), kept from the first tslb_adjoint_force_gradient call until
+    // tslb_destroy: adj_ws_bytes bytes at adj_ws
+    void* adj_ws = nullptr;
+    size_t adj_ws_bytes = 0;
     std::string err;
 };
 
