@@ -92,7 +92,7 @@ def test_taylor_green_200_steps(cuda_ok, kernel):
     # rho - 1 is a small difference of divergence-cancelling mass fluxes; FP32
     # storage and mode rounding of u put its floor near 1e-5 (an FP32 emulation
     # of the same algorithm gives 0.9e-5, FP64 arithmetic with FP32 storage
-    # 0.2e-5).  It is held to 2e-5 and its value is reported in the design doc.
+    # 0.2e-5).  It is held to 2e-5.
     assert_all_below(errs, 2e-5, fields=["drho"])
     mask = interior_mask(dims, (0,) * 6)
     u_scale = np.abs(ref[1]).max()
