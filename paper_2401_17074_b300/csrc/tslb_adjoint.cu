@@ -76,6 +76,10 @@ __global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __r
     for (int f = 0; f < NFIELDS; ++f) gbar[f * g.fstride + n] = gb[f];
 }
 
+// Gather blocks: AX x AY x AZ nodes (x fastest), halo tile HX x HY x HZ.
+constexpr int AX = 32, AY = 4, AZ = 2, AT = AX * AY * AZ;
+constexpr int HX = AX + 2, HY = AY + 2, HZ = AZ + 2, HC = HX * HY * HZ;
+
 // Transpose gather + transpose of post_modes at the source node y, then the
 // Gbar of the preceding step at y (gbar_in belongs to the step m_cur -> m_next,
 // gbar_out to the step before it).
@@ -84,22 +88,38 @@ __global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __r
 // (1, 3, 6 or 10 of them for c with 0, 1, 2 or 3 nonzero components), and
 // adds only to the modes whose weight w(c) phi_k(c) is nonzero (phi_1(0) = 0).
 template <class Codec>
-__global__ void __launch_bounds__(256) adj_gather(const float* __restrict__ gbar,
-                                                  const typename Codec::T* __restrict__ m_cur,
-                                                  float* __restrict__ gbar_out, float* __restrict__ fbar, Geometry g,
-                                                  Physics p) {
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= g.plane * g.nz) return;
-    const int y0 = (int)(n % g.nx), y1 = (int)((n / g.nx) % g.ny), y2 = (int)(n / g.plane);
-    // neighbour offsets per axis (periodic), index c + 1
-    const unsigned X[3] = {(unsigned)(y0 == 0 ? g.nx - 1 : y0 - 1), (unsigned)y0,
-                           (unsigned)(y0 == g.nx - 1 ? 0 : y0 + 1)};
-    const unsigned nx = (unsigned)g.nx, pl = (unsigned)g.plane;
-    const unsigned Y[3] = {nx * (unsigned)(y1 == 0 ? g.ny - 1 : y1 - 1), nx * (unsigned)y1,
-                           nx * (unsigned)(y1 == g.ny - 1 ? 0 : y1 + 1)};
-    const unsigned Z[3] = {pl * (unsigned)(y2 == 0 ? g.nz - 1 : y2 - 1), pl * (unsigned)y2,
-                           pl * (unsigned)(y2 == g.nz - 1 ? 0 : y2 + 1)};
+__global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
+                                                 const typename Codec::T* __restrict__ m_cur,
+                                                 float* __restrict__ gbar_out, float* __restrict__ fbar, Geometry g,
+                                                 Physics p) {
+    // The block's AX x AY x AZ nodes and a one-node halo of Gbar, all ten
+    // fields, staged in shared memory with periodic wrap; the 27 directions
+    // then read it at constant offsets from the thread's cell.
+    __shared__ float tile[NFIELDS * HC];
+    const int tx = threadIdx.x % AX, ty = (threadIdx.x / AX) % AY, tz = threadIdx.x / (AX * AY);
+    const int ox = (int)blockIdx.x * AX, oy = (int)blockIdx.y * AY, oz = (int)blockIdx.z * AZ;  // block origin
     const long long fs = g.fstride;
+    {
+        // one-step wrap holds for coordinates in [-n, 2n): always in y and z
+        // (periodic axes of at least 3 nodes), in x unless the lattice is
+        // narrower than about half a block
+        const bool xwrap1 = ox + AX < 2 * g.nx;
+        for (int c = threadIdx.x; c < HC; c += AT) {
+            const int hx = c % HX, hy = (c / HX) % HY, hz = c / (HX * HY);
+            int gx = ox - 1 + hx, gy = oy - 1 + hy, gz = oz - 1 + hz;
+            gx = xwrap1 ? (gx < 0 ? gx + g.nx : (gx >= g.nx ? gx - g.nx : gx)) : ((gx % g.nx) + g.nx) % g.nx;
+            gy = gy < 0 ? gy + g.ny : (gy >= g.ny ? gy - g.ny : gy);
+            gz = gz < 0 ? gz + g.nz : (gz >= g.nz ? gz - g.nz : gz);
+            const float* G = gbar + ((unsigned)gx + (unsigned)g.nx * (unsigned)gy + (unsigned)g.plane * (unsigned)gz);
+#pragma unroll
+            for (int f = 0; f < NFIELDS; ++f) tile[f * HC + c] = __ldg(G + f * fs);
+        }
+    }
+    __syncthreads();
+    const int px = ox + tx, py = oy + ty, pz = oz + tz;  // this thread's source node
+    if (px >= g.nx || py >= g.ny || pz >= g.nz) return;
+    const long long n = (long long)px + (long long)g.nx * py + g.plane * (long long)pz;
+    const float* Tc = tile + (tz + 1) * (HX * HY) + (ty + 1) * HX + (tx + 1);
     float Ab[NMODES];
 #pragma unroll
     for (int k = 0; k < NMODES; ++k) Ab[k] = 0.0f;
@@ -109,18 +129,18 @@ __global__ void __launch_bounds__(256) adj_gather(const float* __restrict__ gbar
         for (int cy = -1; cy <= 1; ++cy)
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
-                const float* G = gbar + (X[cx + 1] + Y[cy + 1] + Z[cz + 1]);
+                const float* G = Tc + cz * (HX * HY) + cy * HX + cx;
                 // adjoint population: psi(c) . Gbar(y + c), nonzero terms only
-                float gb = __ldg(G);
-                if (cx != 0) gb = fmaf((float)cx, __ldg(G + 1 * fs), gb);
-                if (cy != 0) gb = fmaf((float)cy, __ldg(G + 2 * fs), gb);
-                if (cz != 0) gb = fmaf((float)cz, __ldg(G + 3 * fs), gb);
-                if (cx != 0) gb += __ldg(G + 4 * fs);
-                if (cy != 0) gb += __ldg(G + 5 * fs);
-                if (cz != 0) gb += __ldg(G + 6 * fs);
-                if (cx != 0 && cy != 0) gb = fmaf((float)(cx * cy), __ldg(G + 7 * fs), gb);
-                if (cx != 0 && cz != 0) gb = fmaf((float)(cx * cz), __ldg(G + 8 * fs), gb);
-                if (cy != 0 && cz != 0) gb = fmaf((float)(cy * cz), __ldg(G + 9 * fs), gb);
+                float gb = G[0];
+                if (cx != 0) gb = fmaf((float)cx, G[1 * HC], gb);
+                if (cy != 0) gb = fmaf((float)cy, G[2 * HC], gb);
+                if (cz != 0) gb = fmaf((float)cz, G[3 * HC], gb);
+                if (cx != 0) gb += G[4 * HC];
+                if (cy != 0) gb += G[5 * HC];
+                if (cz != 0) gb += G[6 * HC];
+                if (cx != 0 && cy != 0) gb = fmaf((float)(cx * cy), G[7 * HC], gb);
+                if (cx != 0 && cz != 0) gb = fmaf((float)(cx * cz), G[8 * HC], gb);
+                if (cy != 0 && cz != 0) gb = fmaf((float)(cy * cz), G[9 * HC], gb);
                 const float w = wgt(cx) * wgt(cy) * wgt(cz);
 #pragma unroll
                 for (int k = 0; k < NMODES; ++k) {
@@ -230,7 +250,11 @@ cudaError_t adj_launch_all(const tslb_s* h, int which, const void* a, const void
     const unsigned blocks = (unsigned)((total + 255) / 256);
     typedef typename Codec::T T;
     if (which == 0) adj_seed<Codec><<<blocks, 256, 0, h->stream>>>((const T*)a, c, h->g, p);
-    else adj_gather<Codec><<<blocks, 256, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
+    else {
+        const dim3 grid((unsigned)((h->g.nx + AX - 1) / AX), (unsigned)((h->g.ny + AY - 1) / AY),
+                        (unsigned)((h->g.nz + AZ - 1) / AZ));
+        adj_gather<Codec><<<grid, AT, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
+    }
     return cudaGetLastError();
 }
 
@@ -257,8 +281,8 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
         *msg = "create the handle with options.checkpoint_every > 0";
         return TSLB_ERR_STATE;
     }
-    if (g.plane * g.nz >= (1LL << 31)) {
-        *msg = "the adjoint supports up to 2^31 - 1 nodes";
+    if (g.plane * g.nz >= (1LL << 31) || (g.ny + AY - 1) / AY > 65535 || (g.nz + AZ - 1) / AZ > 65535) {
+        *msg = "the adjoint supports up to 2^31 - 1 nodes, ny <= 262140 and nz <= 131070";
         return TSLB_ERR_UNSUPPORTED;
     }
     if (nsteps <= 0 || nsteps > h->t || (h->t - nsteps) % k != 0) {

@@ -44,6 +44,31 @@ def test_adjoint_matches_complex_step(cuda_ok, n):
         assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (trial, d_adj, d_cs)
 
 
+def test_adjoint_ragged_box_with_force(cuda_ok):
+    """A box that the gather's 32 x 4 x 2 blocks do not tile (70 x 9 x 5: ragged
+    blocks on every axis, x wider than a block, so the halo wraps in one step),
+    a nonzero random force field, and checkpoint segments of 8, 8 and 4 steps."""
+    dims, tau, nsteps = (70, 9, 5), 0.55, 20
+    N = dims[0] * dims[1] * dims[2]
+    state = W.random_state(dims, seed=38, drho=0.002, du=0.02, dpi=1e-4)
+    F0 = (1e-5 * np.random.default_rng(39).uniform(-1, 1, (3, N))).astype(np.float32)
+    s = T.Solver(dims, tau, checkpoint_every=8)
+    s.set_force_field(F0)
+    s.init_moments(*state)
+    s.step(nsteps)
+    g = s.adjoint_force_gradient(nsteps).astype(np.float64)
+    s.close()
+    rng = np.random.default_rng(40)
+    for trial in range(2):
+        v = rng.standard_normal((3, N))
+        h = 1e-30
+        J = oracle.complex_step_energy(dims, tau, (0,) * 6, state[0], state[1], state[2], F0.astype(np.float64),
+                                       h * v, nsteps)
+        d_cs = J.imag / h
+        d_adj = float(np.sum(g * v))
+        assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (trial, d_adj, d_cs)
+
+
 def test_adjoint_partial_window_and_errors(cuda_ok):
     n = 8
     dims, state, s = _setup(n)

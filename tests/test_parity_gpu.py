@@ -47,7 +47,7 @@ def rel_errors(gpu, ref, mask):
 
 
 def run_pair(dims, tau, state, nsteps, kernel, bc=(0,) * 6, force=(0.0, 0.0, 0.0), inflow=None, precision=T.FP32,
-             force_field=None, sponge=None, forcing="luo"):
+             force_field=None, sponge=None, forcing="luo", rounding="nearest"):
     o = oracle.OracleSim(dims, tau, force=force, bc=bc, inflow=inflow, sponge=sponge, forcing=forcing)
     if force_field is not None:  # before the moments: Guo's initial populations depend on it
         o.set_force_field(force_field.astype(np.float64))
@@ -55,7 +55,7 @@ def run_pair(dims, tau, state, nsteps, kernel, bc=(0,) * 6, force=(0.0, 0.0, 0.0
     o.step(nsteps)
     ref = stack(*o.get_moments())
     s = T.Solver(dims, tau, force=force, bc=bc, kernel=kernel, inflow=inflow, precision=precision, sponge=sponge,
-                 forcing=forcing)
+                 forcing=forcing, rounding=rounding, rounding_seed=3)
     s.init_moments(*state)
     if force_field is not None:
         s.set_force_field(force_field.astype(np.float32))
@@ -250,20 +250,25 @@ def test_guo_adjoint_rejected(cuda_ok):
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("prec", [T.BF16, T.FP16], ids=["bf16", "fp16"])
 @pytest.mark.parametrize("case", ["nee-walls", "paper-jet"])
-def test_16bit_storage_faces(cuda_ok, kernel, prec, case):
+@pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
+def test_16bit_storage_faces(cuda_ok, kernel, prec, case, rounding):
     """16-bit storage with the NEE walls and with the paper's jet faces (sponge,
     Gaussian inflow noise).  Each stored value is rounded once per step to
     eps = 2^-9 (BF16) or 2^-12 (FP16) of its scale; a wrong face would show as
-    O(0.1 - 1) errors on its rows, the bound 2e-2 is about ten BF16 roundings."""
+    O(0.1 - 1) errors on its rows, the bound 2e-2 is about ten BF16 roundings.
+    Stochastic rounding errs by up to one spacing instead of half of one, with
+    the same bound."""
     if case == "nee-walls":
         dims, bc = (33, 18, 6), (0, 0, 5, 5, 0, 0)
         state = W.random_state(dims, seed=34)
-        errs, _, _ = run_pair(dims, 0.6, state, 3, kernel, bc=bc, force=(2e-5, 0.0, 0.0), precision=prec)
+        errs, _, _ = run_pair(dims, 0.6, state, 3, kernel, bc=bc, force=(2e-5, 0.0, 0.0), precision=prec,
+                              rounding=rounding)
     else:
         dims, bc = (34, 24, 40), (0, 0, 0, 0, 3, 4)
         inflow = dict(center2=(33, 23), diameter=8, u_jet=0.05, noise_amp=0.01, seed=3, noise="gaussian")
         state = W.random_state(dims, seed=35, drho=0.002, du=0.01, dpi=1e-4)
-        errs, _, _ = run_pair(dims, 0.52, state, 10, kernel, bc=bc, inflow=inflow, sponge=(10, 1000.0), precision=prec)
+        errs, _, _ = run_pair(dims, 0.52, state, 10, kernel, bc=bc, inflow=inflow, sponge=(10, 1000.0), precision=prec,
+                              rounding=rounding)
     assert_all_below(errs, 2e-2)
 
 
