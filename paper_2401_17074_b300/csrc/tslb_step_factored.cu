@@ -105,6 +105,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
         "{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
         : "memory");
 }
+// Arrive only where do_it is set (a predicate instead of a branch).
+__device__ __forceinline__ void mbar_arrive_if(uint64_t* bar, bool do_it) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+        "@q mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)), "r"((unsigned)do_it)
+        : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
@@ -118,8 +125,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 // Bounded wait: gives up after about 2^31 SM clocks, records bit 2 in the
 // device status word and stops waiting for the rest of the launch.
 __device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* err, bool& dead) {
-    if (dead) return;
     if (mbar_try_wait(bar, parity)) return;
+    if (dead) return;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > (1LL << 31)) {
@@ -316,7 +323,7 @@ struct Ctx {
     int tid, lane, warp, x, y, xl, yl;
     unsigned col, plane;
     int z0, z1, np;  // march covers planes z0-1 .. z1 (np of them)
-    bool zper, ybb, store, out_row, row_lo, row_hi, zero_row, nee_row, xlo_mirror, xhi_mirror;
+    bool zper, ybb, store, out_row, row_lo, row_hi, zero_row, nee_row, xlo_mirror, xhi_mirror, arrive;
     int offLv, offRv, offLs, offRs;  // y-exchange read offsets (float4 / float units, relative to a slot base)
 };
 
@@ -436,11 +443,11 @@ struct Kernel {
                 ss[NT + c.tid] = Q[8].pm;
             }
             __syncwarp();
-            if (c.lane == 0 && c.warp != p.drop_row) mbar_arrive(&bars[c.warp * 2 + PAR]);
+            mbar_arrive_if(&bars[c.warp * 2 + PAR], c.arrive);
             {
                 const unsigned par = (unsigned)((j - 2) >> 1) & 1u;  // phase of this buffer's (j-2)/2-th use
-                if (c.warp > 0) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
-                if (c.warp < WROWS - 1) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
+                if (uni(c.warp > 0)) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
+                if (uni(c.warp < WROWS - 1)) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
             }
             // halo and ghost rows only feed the y exchange (warp-uniform)
             if (uni(c.out_row)) {
@@ -632,6 +639,7 @@ __global__ void __launch_bounds__(NT, 1)
     c.row_hi = c.y == g.ny - 1;
     c.zero_row = c.ybb && (c.y == -1 || c.y == g.ny);
     c.nee_row = NEEY && (c.y == -1 || c.y == g.ny);
+    c.arrive = c.lane == 0 && c.warp != p.drop_row;
     // y-exchange read offsets: the row below / above, or -- on a free-slip wall
     // row -- the node's own value of the opposite population (p- slots sit
     // 2 float4 slots after the p+ slots, the scalar p- one float slot after p+)
