@@ -142,7 +142,8 @@ typedef struct tslb_options {
     void* stream;         /* cudaStream_t to run on; NULL = a stream owned by the handle */
     int device;           /* CUDA device ordinal, default 0 */
     int kernel;           /* tslb_kernel, default TSLB_KERNEL_AUTO */
-    int checkpoint_every; /* >0: tslb_step records a moment checkpoint every k steps (adjoint) */
+    int checkpoint_every; /* >0: tslb_step records a moment checkpoint every k steps (adjoint); the
+                           * checkpoint buffers are reused by later runs until tslb_destroy */
     tslb_inflow inflow;   /* used when bc[4] == TSLB_BC_INFLOW */
     /* Sponge layer towards the z+ face (the jet's exit, Sec. 3.2): with
      * W = sponge_width > 0 (default 0 = none) and z_s = nz - W, a node at

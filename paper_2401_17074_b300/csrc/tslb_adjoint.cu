@@ -289,7 +289,7 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
         *msg = "nsteps must be in (0, steps taken] with (steps taken - nsteps) a multiple of checkpoint_every";
         return TSLB_ERR_INVALID;
     }
-    if ((int64_t)h->ckpts.size() * k < h->t) {
+    if (h->ckpt_valid * k < h->t) {
         *msg = "missing checkpoints";
         return TSLB_ERR_STATE;
     }

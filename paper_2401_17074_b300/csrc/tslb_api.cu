@@ -132,11 +132,9 @@ namespace {
 
 size_t state_bytes(const tslb_s* h) { return (size_t)h->nfields * h->g.fstride * h->elem; }
 
-void drop_checkpoints(tslb_s* h) {
-    if (!h->ckpts.empty()) cudaStreamSynchronize(h->stream);
-    for (void* c : h->ckpts) cudaFree(c);
-    h->ckpts.clear();
-}
+// Forget the recorded checkpoints; their buffers are reused by the next run
+// (copies into them are ordered on the handle's stream).
+void drop_checkpoints(tslb_s* h) { h->ckpt_valid = 0; }
 
 }  // namespace
 
@@ -421,13 +419,17 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
     const int k = h->checkpoint_every;
     for (int64_t s = 0; s < nsteps; ++s) {
         cudaError_t e;
-        if (k > 0 && h->t % k == 0 && (int64_t)h->ckpts.size() == h->t / k) {
-            void* c = nullptr;
-            e = dev_alloc(&c, state_bytes(h));
-            if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "checkpoint allocation failed");
-            h->ckpts.push_back(c);
+        if (k > 0 && h->t % k == 0 && h->ckpt_valid == h->t / k) {
+            if ((size_t)h->ckpt_valid == h->ckpts.size()) {
+                void* c = nullptr;
+                e = dev_alloc(&c, state_bytes(h));
+                if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "checkpoint allocation failed");
+                h->ckpts.push_back(c);
+            }
+            void* c = h->ckpts[(size_t)h->ckpt_valid];
             e = cudaMemcpyAsync(c, h->buf[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint copy");
+            ++h->ckpt_valid;
         }
         const tslb::Physics p = tslb::make_physics(h);
         e = tslb::launch_step_any(h, h->buf[h->cur], h->buf[h->cur ^ 1], p);

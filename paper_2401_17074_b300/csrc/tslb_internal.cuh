@@ -525,7 +525,10 @@ struct tslb_s {
     int diag_blocks = 0;
     double* diag_host = nullptr;
     // adjoint checkpoints: ckpts[s] holds the moments at step s * checkpoint_every
+    // for s < ckpt_valid; the buffers stay allocated for reuse by later runs
+    // (tslb_init_moments only resets ckpt_valid) until tslb_destroy
     std::vector<void*> ckpts;
+    int64_t ckpt_valid = 0;
     // adjoint workspace (two Gbar arrays, the force gradient, one recomputed
     // segment), kept from the first tslb_adjoint_force_gradient call until
     // tslb_destroy: adj_ws_bytes bytes at adj_ws
