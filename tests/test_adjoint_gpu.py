@@ -44,6 +44,58 @@ def test_adjoint_matches_complex_step(cuda_ok, n):
         assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (trial, d_adj, d_cs)
 
 
+def _oracle_energy(dims, tau, state, F, nsteps):
+    o = oracle.OracleSim(dims, tau)
+    o.init_moments(*state)
+    o.set_force_field(F)
+    o.step(nsteps)
+    r, u, _ = o.get_moments()
+    return 0.5 * float(np.sum(r * (u ** 2).sum(0)))
+
+
+def test_adjoint_matches_central_differences(cuda_ok):
+    """16^3, 64 steps: the GPU adjoint's directional derivative against FP64
+    central differences of the oracle, (J(F + eps v) - J(F - eps v)) / (2 eps)
+    with eps = 1e-6 (truncation O(eps^2), far below the bound)."""
+    n, nsteps, tau = 16, 64, 0.52
+    dims, state, s = _setup(n, nsteps=nsteps, tau=tau)
+    N = n ** 3
+    F0 = np.zeros((3, N), dtype=np.float32)
+    s.init_moments(*state)
+    s.set_force_field(F0)
+    s.step(nsteps)
+    g = s.adjoint_force_gradient(nsteps).astype(np.float64)
+    s.close()
+    v = np.random.default_rng(18).standard_normal((3, N))
+    eps = 1e-6
+    d_fd = (_oracle_energy(dims, tau, state, eps * v, nsteps) - _oracle_energy(dims, tau, state, -eps * v, nsteps)) / (
+        2 * eps)
+    d_adj = float(np.sum(g * v))
+    assert abs(d_adj - d_fd) <= 1e-4 * abs(d_fd), (d_adj, d_fd)
+
+
+def test_adjoint_matches_complex_step_128(cuda_ok):
+    """The full-size adjoint workload: 128^3, 64 steps, checkpoints every 16,
+    one random direction against the oracle's complex-step derivative (about a
+    minute of host time for the complex-step run)."""
+    n, nsteps, tau = 128, 64, 0.52
+    dims, state, s = _setup(n, nsteps=nsteps, tau=tau)
+    N = n ** 3
+    F0 = np.zeros((3, N), dtype=np.float32)
+    s.init_moments(*state)
+    s.set_force_field(F0)
+    s.step(nsteps)
+    g = s.adjoint_force_gradient(nsteps).astype(np.float64)
+    s.close()
+    v = np.random.default_rng(17).standard_normal((3, N))
+    h = 1e-30
+    J = oracle.complex_step_energy(dims, tau, (0,) * 6, state[0], state[1], state[2], F0.astype(np.float64), h * v,
+                                   nsteps)
+    d_cs = J.imag / h
+    d_adj = float(np.sum(g * v))
+    assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (d_adj, d_cs)
+
+
 def test_adjoint_ragged_box_with_force(cuda_ok):
     """A box that the gather's 32 x 4 x 2 blocks do not tile (70 x 9 x 5: ragged
     blocks on every axis, x wider than a block, so the halo wraps in one step),
