@@ -67,19 +67,21 @@ _lib = None
 
 
 def lib_path():
-    return _build.LIB
+    """libtslb.so, or with TSLB_CHECKED=1 its index-checked build libtslb_checked.so."""
+    return _build.LIB_CHECKED if os.environ.get("TSLB_CHECKED") == "1" else _build.LIB
 
 
 def load(build_if_missing=True):
-    """Load libtslb.so (building it first if the sources are newer)."""
+    """Load the library (building it first if the sources are newer)."""
     global _lib
     if _lib is not None:
         return _lib
     if build_if_missing:
         _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError("libtslb.so is missing; run paper_2401_17074_b300.build.build()")
-    L = ctypes.CDLL(_build.LIB)
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("%s is missing; run paper_2401_17074_b300.build.build()" % os.path.basename(path))
+    L = ctypes.CDLL(path)
     vp, i64, dp, fp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
     L.tslb_options_default.argtypes = [ctypes.POINTER(tslb_options)]
     L.tslb_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(i64), ctypes.c_double, dp,

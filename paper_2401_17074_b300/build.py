@@ -1,4 +1,16 @@
-"""Build step of the TSLB CUDA library: nvcc -> libtslb.so, in-tree, for sm_103a."""
+"""Build step of the TSLB CUDA library, in-tree, for sm_103a.
+
+Two variants of the same sources:
+  libtslb.so          the product library;
+  libtslb_checked.so  -DTSLB_CHECKED: every kernel tests its global-memory
+                      indices and, on one out of range, records bit 4 of the
+                      device status word and skips the access instead of
+                      faulting (the stand-in for a memory checker; selected at
+                      load time with TSLB_CHECKED=1).
+Each source compiles to an object under _build/ (in parallel), then nvcc links
+the shared library.
+"""
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -6,7 +18,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtslb.so")
+LIB_CHECKED = os.path.join(HERE, "libtslb_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+OBJDIR = os.path.join(HERE, "_build")
 
 SOURCES = [
     "tslb_api.cu",
@@ -18,36 +32,61 @@ SOURCES = [
     "tslb_step2d.cu",
 ]
 
-NVCC_FLAGS = [
-    "-gencode", "arch=compute_103a,code=sm_103a",
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + [
     "-O3", "-lineinfo", "-std=c++17",
-    "-shared", "-Xcompiler", "-fPIC",
+    "-Xcompiler", "-fPIC",
     "-Xptxas", "-v",
 ]
 
+VARIANTS = {LIB: [], LIB_CHECKED: ["-DTSLB_CHECKED"]}
 
-def _stale():
-    if not os.path.exists(LIB):
+
+def _stale(lib):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "tslb.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _compile(nvcc, src, obj, defs):
+    cmd = [nvcc] + NVCC_FLAGS + defs + ["-I", INCLUDE, "-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    return r.returncode, src, r.stdout + r.stderr
+
+
 def build(force=False, verbose=False):
-    """Compile csrc/*.cu into libtslb.so next to this file (no-op when up to date)."""
-    if not force and not _stale():
+    """Compile csrc/*.cu into libtslb.so and libtslb_checked.so next to this
+    file (each only when out of date unless force).  Returns the product path."""
+    todo = [lib for lib in VARIANTS if force or _stale(lib)]
+    if not todo:
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    cmd = [nvcc] + NVCC_FLAGS + ["-I", INCLUDE, "-o", LIB + ".tmp"] + srcs
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libtslb.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
-    os.replace(LIB + ".tmp", LIB)
+    os.makedirs(OBJDIR, exist_ok=True)
+    jobs = []
+    for lib in todo:
+        tag = os.path.splitext(os.path.basename(lib))[0]
+        for s in SOURCES:
+            obj = os.path.join(OBJDIR, "%s.%s.o" % (tag, os.path.splitext(s)[0]))
+            jobs.append((lib, os.path.join(CSRC, s), obj))
+    workers = max(1, min(len(jobs), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda j: _compile(nvcc, j[1], j[2], VARIANTS[j[0]]), jobs))
+    for rc, src, log in results:
+        if rc != 0:
+            sys.stderr.write(log)
+            raise RuntimeError("nvcc failed compiling %s" % os.path.basename(src))
+        if verbose:
+            sys.stderr.write(log)
+    for lib in todo:
+        objs = [j[2] for j in jobs if j[0] == lib]
+        r = subprocess.run([nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", lib + ".tmp"] + objs,
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout + r.stderr)
+            raise RuntimeError("nvcc failed linking %s" % os.path.basename(lib))
+        os.replace(lib + ".tmp", lib)
     return LIB
 
 

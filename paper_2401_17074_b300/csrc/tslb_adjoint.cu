@@ -19,6 +19,8 @@
 
 #include "tslb_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace tslb {
 namespace {
 
@@ -110,9 +112,11 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
             gx = xwrap1 ? (gx < 0 ? gx + g.nx : (gx >= g.nx ? gx - g.nx : gx)) : ((gx % g.nx) + g.nx) % g.nx;
             gy = gy < 0 ? gy + g.ny : (gy >= g.ny ? gy - g.ny : gy);
             gz = gz < 0 ? gz + g.nz : (gz >= g.nz ? gz - g.nz : gz);
-            const float* G = gbar + ((unsigned)gx + (unsigned)g.nx * (unsigned)gy + (unsigned)g.plane * (unsigned)gz);
+            const unsigned gi = (unsigned)gx + (unsigned)g.nx * (unsigned)gy + (unsigned)g.plane * (unsigned)gz;
+            const float* G = gbar + gi;
+            const bool ok = TSLB_IN_RANGE(gi, g.plane * g.nz, p.err);
 #pragma unroll
-            for (int f = 0; f < NFIELDS; ++f) tile[f * HC + c] = __ldg(G + f * fs);
+            for (int f = 0; f < NFIELDS; ++f) tile[f * HC + c] = ok ? __ldg(G + f * fs) : 0.0f;
         }
     }
     __syncthreads();
@@ -329,6 +333,7 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
         const int64_t s = (n_end - 1) / k;
         const int64_t n_beg = s * k;
         const int64_t len = n_end - n_beg;
+        nvtxRangePushA("adjoint segment: recompute and backward sweep");
         e = cudaMemcpyAsync(seg, h->ckpts[s], state_bytes, cudaMemcpyDeviceToDevice, h->stream);
         // states n_beg .. n_end - 1 (the gather of step n needs m(n) only)
         for (int64_t j = 0; j + 1 < len && e == cudaSuccess; ++j) {
@@ -342,6 +347,7 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
             e = adj_launch(h, 1, m_cur, gbar[cur], gbar[cur ^ 1], fbar, p);
             cur ^= 1;
         }
+        nvtxRangePop();
         n_end = n_beg;
     }
     // scatter the interior gradient into the full-lattice [3][N] output

@@ -8,6 +8,21 @@
 #include <vector>
 
 #include "tslb_internal.cuh"
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+
+// NVTX range around a host call (visible in Nsight Systems / ncu range filters;
+// a no-op unless a tool is attached).  For the asynchronous calls it covers the
+// host side: argument checks and the launches.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -51,8 +66,9 @@ cudaError_t dev_alloc_async(void** p, size_t bytes, cudaStream_t s) {
 
 bool valid_handle(const tslb_s* h) { return h != nullptr; }
 
-// After a synchronise: report a bounded device wait that gave up (the kernel
-// then skipped the rest of its work), and clear the word.
+// After a synchronise: report a bounded device wait that gave up (bit 2; the
+// kernel then skipped the rest of its work) or, in the checked build, an index
+// out of range (bit 4; the access was skipped), and clear the word.
 int check_device_status(tslb_s* h) {
     int v = 0;
     if (!h->dev_err) return TSLB_OK;
@@ -60,7 +76,10 @@ int check_device_status(tslb_s* h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "status read");
     if (v != 0) {
         cudaMemset(h->dev_err, 0, sizeof(int));
-        return fail(h, TSLB_ERR_CUDA, "a bounded device wait gave up; the step results are invalid");
+        std::string m;
+        if (v & 2) m += "a bounded device wait gave up; ";
+        if (v & TSLB_ERR_BIT_INDEX) m += "an index check of the checked build failed; ";
+        return fail(h, TSLB_ERR_CUDA, m + "the step results are invalid");
     }
     return TSLB_OK;
 }
@@ -155,6 +174,7 @@ int tslb_options_default(tslb_options* opt) {
 
 int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, const double force[3],
                 const int bc[6], const tslb_options* opt) {
+    const Range range("tslb_create");
     g_create_error.clear();
     if (!out || !dims || !bc) return fail(nullptr, TSLB_ERR_INVALID, "null argument");
     if (lattice != TSLB_D3Q27 && lattice != TSLB_D2Q9)
@@ -339,6 +359,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
 }
 
 int tslb_init_moments(tslb_t* h, const double* rho, const double* u, const double* pi, int where) {
+    const Range range("tslb_init_moments");
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (!rho || !u) return fail(h, TSLB_ERR_INVALID, "rho and u are required");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
@@ -371,6 +392,7 @@ int tslb_init_moments(tslb_t* h, const double* rho, const double* u, const doubl
 }
 
 int tslb_set_force_field(tslb_t* h, const float* F, int where) {
+    const Range range("tslb_set_force_field");
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
     if (h->lattice == TSLB_D2Q9) return fail(h, TSLB_ERR_UNSUPPORTED, "D2Q9 takes the constant body force only");
@@ -411,6 +433,7 @@ int tslb_set_force_field(tslb_t* h, const float* F, int where) {
 }
 
 int tslb_step(tslb_t* h, int64_t nsteps) {
+    const Range range("tslb_step");
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (nsteps < 0) return fail(h, TSLB_ERR_INVALID, "nsteps < 0");
     cudaSetDevice(h->device);
@@ -441,6 +464,7 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
 }
 
 int tslb_get_moments(tslb_t* h, double* rho, double* u, double* pi, int where) {
+    const Range range("tslb_get_moments");
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
     cudaSetDevice(h->device);
@@ -471,6 +495,7 @@ int tslb_get_moments(tslb_t* h, double* rho, double* u, double* pi, int where) {
 }
 
 int tslb_diagnostics(tslb_t* h, tslb_diag* out) {
+    const Range range("tslb_diagnostics");
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (!out) return fail(h, TSLB_ERR_INVALID, "null output");
     cudaSetDevice(h->device);
@@ -499,6 +524,7 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out) {
 }
 
 int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where) {
+    const Range range("tslb_adjoint_force_gradient");
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (!dJdF) return fail(h, TSLB_ERR_INVALID, "null output");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");

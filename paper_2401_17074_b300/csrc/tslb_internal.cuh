@@ -100,6 +100,24 @@ __host__ __device__ __forceinline__ uint32_t sr_step_key(unsigned long long seed
     return mix32((uint32_t)seed ^ mix32((uint32_t)t ^ mix32((uint32_t)(seed >> 32) ^ 0x5bd1e995U)));
 }
 
+// ---- checked build ------------------------------------------------------------
+// With -DTSLB_CHECKED the kernels test each global-memory index (and the step
+// kernel its shared-memory exchange offsets) before the access; an index out
+// of range sets bit 4 of the device status word and the access is skipped, so
+// a wrong index shows as a reported error instead of a memory fault.  The
+// product build compiles every test to `true`.
+#define TSLB_ERR_BIT_INDEX 4
+#ifdef TSLB_CHECKED
+__device__ __forceinline__ bool checked_in_range(long long i, long long n, int* err) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicOr(err, TSLB_ERR_BIT_INDEX);
+    return false;
+}
+#define TSLB_IN_RANGE(i, n, err) ::tslb::checked_in_range((long long)(i), (long long)(n), (err))
+#else
+#define TSLB_IN_RANGE(i, n, err) true
+#endif
+
 // ---- storage ----------------------------------------------------------------
 // One moment buffer holds three arrays of small vectors, one entry per stored
 // (interior) node, x fastest:

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NT2) step2d_kernel(const float* __restrict__ s
         const int yl = row_of(y0 - 1 + j);
         const unsigned n = xl + (unsigned)g.nx * (unsigned)(yl < 0 ? 0 : yl);
         char* b = slot0 + (j & (SLOTS2 - 1)) * (NT2 * ROWB);
-        if (j < np && yl >= 0) {
+        if (j < np && yl >= 0 && TSLB_IN_RANGE(n, g.plane, p.err)) {
             cp_async2<16>(smem_addr(b), src + (size_t)n * 4);
             cp_async2<8>(smem_addr(b + 16), src + 4 * fs + (size_t)n * 2);
         }
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(NT2) step2d_kernel(const float* __restrict__ s
             //      Pi_ab = (S_ab - J_a u_b - delta_ab D0/3) / 36
             const float inv = rcp_refined(36.0f + D0);
             const float ux = Jx * inv, uy = Jy * inv, d3 = D0 * (1.0f / 3.0f);
-            if (store) {
+            if (store && TSLB_IN_RANGE(xl + (long long)g.nx * yo, g.plane, p.err)) {
                 const unsigned n = xl + (unsigned)g.nx * (unsigned)yo;
                 reinterpret_cast<float4*>(dst)[n] =
                     make_float4(ux, uy, div36(D0), div36(Sxy - Jx * uy));

@@ -24,6 +24,11 @@ template <class Codec>
 __device__ __forceinline__ void node_modes(const typename Codec::T* __restrict__ src, const Geometry& g,
                                            const Physics& p, long long idx, int zfull, float A[NMODES]) {
     float m[NFIELDS];
+    if (!TSLB_IN_RANGE(idx, g.plane * g.nz, p.err)) {
+#pragma unroll
+        for (int k = 0; k < NMODES; ++k) A[k] = 0.0f;
+        return;
+    }
     load_node<Codec>(src, g, p, idx, m);
     float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
     if (p.force) {
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
         }
         guo_finish(out, F0, F1, F2, 1.0f);
     }
-    NodeIO<Codec>::store(dst, g.fstride, n, p, out);
+    if (TSLB_IN_RANGE(n, g.plane * g.nz, p.err)) NodeIO<Codec>::store(dst, g.fstride, n, p, out);
 }
 
 }  // namespace

@@ -306,7 +306,7 @@ __device__ __forceinline__ void load_force(const Physics& p, const Geometry& g, 
     F0 = p.F[0];
     F1 = p.F[1];
     F2 = p.F[2];
-    if (p.force) {
+    if (p.force && TSLB_IN_RANGE(idx, g.plane * g.nz, p.err)) {
         F0 = __ldg(p.force + idx);
         F1 = __ldg(p.force + g.fstride + idx);
         F2 = __ldg(p.force + 2 * g.fstride + idx);
@@ -335,6 +335,9 @@ struct Ctx {
     // wait flags voted at set-up)
     bool zper, ybb, store, out_row, row_lo, row_hi, zero_row, nee_row, xlo_mirror, xhi_mirror, arrive, wait_lo, wait_hi;
     int offLv, offRv, offLs, offRs;  // y-exchange read offsets (float4 / float units, relative to a slot base)
+#ifdef TSLB_CHECKED
+    int* err;  // device status word, for the index checks
+#endif
 };
 
 template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO>
@@ -354,9 +357,11 @@ struct Kernel {
                                                           char* pfb, int zl) {
         const unsigned n = c.col + c.plane * (unsigned)zl;
         char* b = pfb + PAR * PF::BUF;
-        cp_async<PF::B01>(smem_u32(b + c.tid * PF::B01), src + (size_t)n * 4);
-        cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * g.fstride + (size_t)n * 4);
-        cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * g.fstride + (size_t)n * 2);
+        if (TSLB_IN_RANGE(n, g.plane * g.nz, c.err)) {
+            cp_async<PF::B01>(smem_u32(b + c.tid * PF::B01), src + (size_t)n * 4);
+            cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * g.fstride + (size_t)n * 4);
+            cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * g.fstride + (size_t)n * 2);
+        }
         cp_async_commit();
     }
     template <int PAR>
@@ -380,8 +385,10 @@ struct Kernel {
         const unsigned idx = c.col + c.plane * (unsigned)zl;
         // (1 - omega) s_pi of this source plane: uniform, or the sponge layer's
         // value at the plane's lattice z (ghost planes included)
-        const float om_pi = SPONGE ? __ldg(p.omega1_z + ((!STEADY && c.zper) ? zl : zs + g.lo[2])) * p.s_pi
-                                   : p.omega1_pi;
+        const int zfull = (!STEADY && c.zper) ? zl : zs + g.lo[2];  // lattice z of the source plane
+        const float om_pi = (SPONGE && TSLB_IN_RANGE(zfull, g.nz + 2 * g.lo[2], p.err))
+                                ? __ldg(p.omega1_z + zfull) * p.s_pi
+                                : p.omega1_pi;
         // next plane's copies go out before this plane's are consumed
         if (STEADY) prefetch_plane<PAR ^ 1>(c, g, src, pfb, zs + 1);
         else if (zs < c.z1) prefetch<PAR ^ 1>(c, g, src, pfb, j + 1);
@@ -548,7 +555,8 @@ struct Kernel {
                     load_force(p, g, oidx, G0, G1, G2);
                     guo_finish(out, G0, G1, G2, sizeof(T) == 4 ? 1.0f : p.inv_s_pi);
                 }
-                if (c.store) NodeIO<Codec>::store_rawpi(dst, g.fstride, oidx, p, out);
+                if (c.store && TSLB_IN_RANGE(oidx, g.plane * g.nz, p.err))
+                    NodeIO<Codec>::store_rawpi(dst, g.fstride, oidx, p, out);
             }
         }
         // ---- advance the z window --------------------------------------------
@@ -669,6 +677,15 @@ __global__ void __launch_bounds__(NT, 1)
     c.offRv = (yfs && c.row_hi) ? c.tid - 2 * NT : above;
     c.offLs = (yfs && c.row_lo) ? NT + c.tid : below;
     c.offRs = (yfs && c.row_hi) ? c.tid - NT : above;
+#ifdef TSLB_CHECKED
+    c.err = p.err;
+    // every exchange read: float4 slots q * NT + off (q = 0, 1 below, 2, 3
+    // above) in [0, YV * NT), float slots off and NT + off in [0, 2 * NT)
+    if (!(TSLB_IN_RANGE(c.offLv, YV * NT - NT, p.err) && TSLB_IN_RANGE(2 * NT + c.offRv, YV * NT - NT, p.err) &&
+          TSLB_IN_RANGE(c.offLs, 2 * NT, p.err) && TSLB_IN_RANGE(NT + c.offRs, 2 * NT, p.err))) {
+        c.offLv = c.offRv = c.offLs = c.offRs = c.tid;
+    }
+#endif
     c.z0 = (int)blockIdx.z * zchunk;
     c.z1 = min(c.z0 + zchunk, g.nz);
     c.np = c.z1 - c.z0 + 2;
