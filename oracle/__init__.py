@@ -19,7 +19,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tslb_oracle.cpp")
 _SRC2 = os.path.join(_HERE, "tslb_oracle2d.cpp")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# ORACLE_SANITIZE=1 selects a build with AddressSanitizer and
+# UndefinedBehaviorSanitizer (the process must preload the ASan runtime).
+_SANITIZE = os.environ.get("ORACLE_SANITIZE") == "1"
+_LIB = os.path.join(_HERE, "liboracle_san.so" if _SANITIZE else "liboracle.so")
 
 PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL = 0, 1, 2, 3, 4, 5
 
@@ -27,11 +30,13 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the oracle shared library with g++ -O3 -fopenmp."""
+    """Compile the oracle shared library with g++ -O3 -fopenmp (sanitized: -O1 with ASan and UBSan)."""
     stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(p) for p in (_SRC, _SRC2))
     if force or stale:
-        subprocess.check_call(["g++", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c++17",
-                               "-o", _LIB, _SRC, _SRC2])
+        opt = (["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                "-fno-sanitize-recover=undefined"] if _SANITIZE else ["-O3"])
+        subprocess.check_call(["g++"] + opt + ["-fopenmp", "-fPIC", "-shared", "-std=c++17",
+                                               "-o", _LIB, _SRC, _SRC2])
     return _LIB
 
 
