@@ -67,7 +67,10 @@ _lib = None
 
 
 def lib_path():
-    """libtslb.so, or with TSLB_CHECKED=1 its index-checked build libtslb_checked.so."""
+    """libtslb.so; with TSLB_CHECKED=1 its index-checked build libtslb_checked.so,
+    with TSLB_HOSTSAN=1 its host-sanitized build libtslb_hostsan.so."""
+    if os.environ.get("TSLB_HOSTSAN") == "1":
+        return _build.LIB_HOSTSAN
     return _build.LIB_CHECKED if os.environ.get("TSLB_CHECKED") == "1" else _build.LIB
 
 

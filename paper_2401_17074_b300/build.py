@@ -19,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtslb.so")
 LIB_CHECKED = os.path.join(HERE, "libtslb_checked.so")
+LIB_HOSTSAN = os.path.join(HERE, "libtslb_hostsan.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OBJDIR = os.path.join(HERE, "_build")
 
@@ -40,6 +41,11 @@ NVCC_FLAGS = ARCH + [
 ]
 
 VARIANTS = {LIB: [], LIB_CHECKED: ["-DTSLB_CHECKED"]}
+# Host code under AddressSanitizer / UndefinedBehaviorSanitizer (device code
+# unchanged); built on demand by the CPU test of the ABI's host paths and
+# selected with TSLB_HOSTSAN=1 (the process must preload the ASan runtime).
+HOSTSAN_FLAGS = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+                 "-Xcompiler", "-fno-omit-frame-pointer"]  # one flag each: nvcc splits -Xcompiler at commas
 
 
 def _stale(lib):
@@ -56,10 +62,12 @@ def _compile(nvcc, src, obj, defs):
     return r.returncode, src, r.stdout + r.stderr
 
 
-def build(force=False, verbose=False):
+def build(force=False, verbose=False, variants=None):
     """Compile csrc/*.cu into libtslb.so and libtslb_checked.so next to this
-    file (each only when out of date unless force).  Returns the product path."""
-    todo = [lib for lib in VARIANTS if force or _stale(lib)]
+    file (each only when out of date unless force).  Returns the product path.
+    variants: a {library path: extra nvcc flags} map to build instead."""
+    variants = VARIANTS if variants is None else variants
+    todo = [lib for lib in variants if force or _stale(lib)]
     if not todo:
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
@@ -72,7 +80,7 @@ def build(force=False, verbose=False):
             jobs.append((lib, os.path.join(CSRC, s), obj))
     workers = max(1, min(len(jobs), os.cpu_count() or 1))
     with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
-        results = list(ex.map(lambda j: _compile(nvcc, j[1], j[2], VARIANTS[j[0]]), jobs))
+        results = list(ex.map(lambda j: _compile(nvcc, j[1], j[2], variants[j[0]]), jobs))
     for rc, src, log in results:
         if rc != 0:
             sys.stderr.write(log)
@@ -81,13 +89,20 @@ def build(force=False, verbose=False):
             sys.stderr.write(log)
     for lib in todo:
         objs = [j[2] for j in jobs if j[0] == lib]
-        r = subprocess.run([nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", lib + ".tmp"] + objs,
-                           capture_output=True, text=True)
+        link_extra = HOSTSAN_FLAGS if variants[lib] == HOSTSAN_FLAGS else []
+        r = subprocess.run([nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC"] + link_extra + ["-o", lib + ".tmp"]
+                           + objs, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("nvcc failed linking %s" % os.path.basename(lib))
         os.replace(lib + ".tmp", lib)
     return LIB
+
+
+def build_hostsan():
+    """libtslb_hostsan.so: the library with its host code sanitized."""
+    build(variants={LIB_HOSTSAN: HOSTSAN_FLAGS})
+    return LIB_HOSTSAN
 
 
 if __name__ == "__main__":
