@@ -32,7 +32,7 @@ namespace tslb {
 namespace {
 
 constexpr int XOUT2 = 30;   // output columns per warp (lanes 1..30)
-constexpr int WARPS2 = 4;   // independent warps per CTA
+constexpr int WARPS2 = 8;   // independent warps per CTA
 constexpr int SLOTS2 = 4;   // prefetch ring (rows)
 constexpr int AHEAD2 = 3;   // rows fetched ahead
 constexpr int NT2 = 32 * WARPS2;
@@ -51,7 +51,7 @@ __device__ __forceinline__ void cp_async2(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void commit2() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void wait_ahead2() { asm volatile("cp.async.wait_group 3;" ::: "memory"); }
+__device__ __forceinline__ void wait_ahead2() { asm volatile("cp.async.wait_group %0;" ::"n"(AHEAD2) : "memory"); }
 
 struct Pops1 {
     float pp, pm, c;
