@@ -32,7 +32,7 @@ namespace tslb {
 namespace {
 
 constexpr int XOUT2 = 30;   // output columns per warp (lanes 1..30)
-constexpr int WARPS2 = 8;   // independent warps per CTA
+constexpr int WARPS2 = 16;   // independent warps per CTA
 constexpr int SLOTS2 = 4;   // prefetch ring (rows)
 constexpr int AHEAD2 = 3;   // rows fetched ahead
 constexpr int NT2 = 32 * WARPS2;
