@@ -47,7 +47,10 @@ typedef enum tslb_status {
     TSLB_OK = 0,
     TSLB_ERR_INVALID = -1,     /* bad argument (null pointer, tau <= 1/2, size too small, ...) */
     TSLB_ERR_UNSUPPORTED = -2, /* valid request this library does not implement */
-    TSLB_ERR_CUDA = -3,        /* a CUDA runtime call failed; see tslb_last_error */
+    TSLB_ERR_CUDA = -3,        /* a CUDA runtime call failed, or a kernel reported through the device
+                                * status word: a bounded wait that gave up (the factored step's row
+                                * exchange) or, in the index-checked build libtslb_checked.so, an
+                                * index out of range; see tslb_last_error */
     TSLB_ERR_ALLOC = -4,       /* device or host allocation failed */
     TSLB_ERR_UNSTABLE = -5,    /* diagnostics found NaN/Inf in the moment fields */
     TSLB_ERR_STATE = -6        /* call not valid in the handle's current state */
@@ -254,7 +257,9 @@ int tslb_diagnostics_noalloc(const double* rho, const double* u, const double* p
 /* Number of interior (updated) nodes. */
 int64_t tslb_interior_nodes(const tslb_t* h);
 
-/* Block until all work queued on the handle's stream is done. */
+/* Block until all work queued on the handle's stream is done, then report the
+ * device status word (TSLB_ERR_CUDA if a kernel recorded a failure since the
+ * last report; the word is cleared). */
 int tslb_synchronize(tslb_t* h);
 
 /* Release all memory of the handle.  NULL is ignored. */
