@@ -435,32 +435,44 @@ def time_adjoint(T, torch, stream, n=128, nsteps=64, k=16, tau=0.52):
             "note": "wall clock; the adjoint recomputes each checkpoint segment"}
 
 
-def time_e2e(T, torch, prm, state, steps, stream):
-    """End to end through the C ABI: pinned host FP64 moments in, K steps, moments back to pinned host."""
+def time_e2e(T, torch, prm, state, steps, stream, fp32_io=True):
+    """End to end through the C ABI: moments in from pinned host memory, K steps,
+    moments back to pinned host memory, wall clock.  fp32_io: the FP32 host
+    interface (drho = rho - 1, u, Pi as FP32, tslb_init_moments_f32 /
+    tslb_get_moments_f32: 40 B per node each way); else the FP64 one (80 B)."""
     rho, u, pi = state
     N = rho.size
-    h_rho = torch.from_numpy(rho).pin_memory()
-    h_u = torch.from_numpy(u.reshape(-1)).pin_memory()
-    h_pi = torch.from_numpy(pi.reshape(-1)).pin_memory()
-    o_rho = torch.empty(N, dtype=torch.float64).pin_memory()
-    o_u = torch.empty(3 * N, dtype=torch.float64).pin_memory()
-    o_pi = torch.empty(6 * N, dtype=torch.float64).pin_memory()
+    if fp32_io:
+        dt, init, get = torch.float32, T.tslb_init_moments_f32, T.tslb_get_moments_f32
+        first = (rho - 1.0).astype(np.float32)
+        u_in, pi_in = u.astype(np.float32), pi.astype(np.float32)
+    else:
+        dt, init, get = torch.float64, T.tslb_init_moments, T.tslb_get_moments
+        first, u_in, pi_in = rho, u, pi
+    h_first = torch.from_numpy(first).pin_memory()
+    h_u = torch.from_numpy(u_in.reshape(-1)).pin_memory()
+    h_pi = torch.from_numpy(pi_in.reshape(-1)).pin_memory()
+    o_first = torch.empty(N, dtype=dt).pin_memory()
+    o_u = torch.empty(3 * N, dtype=dt).pin_memory()
+    o_pi = torch.empty(6 * N, dtype=dt).pin_memory()
     s = T.Solver(prm["dims"], prm["tau"], force=prm["force"], bc=prm["bc"], stream=stream.cuda_stream)
     # one untimed pass to settle allocator pools
-    T.tslb_init_moments(s.handle, h_rho, h_u, h_pi)
+    init(s.handle, h_first, h_u, h_pi)
     s.step(2)
-    T.tslb_get_moments(s.handle, o_rho, o_u, o_pi, T.HOST)
+    get(s.handle, o_first, o_u, o_pi, T.HOST)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    T.tslb_init_moments(s.handle, h_rho, h_u, h_pi)
+    init(s.handle, h_first, h_u, h_pi)
     s.step(steps)
-    T.tslb_get_moments(s.handle, o_rho, o_u, o_pi, T.HOST)
+    get(s.handle, o_first, o_u, o_pi, T.HOST)
     el = time.perf_counter() - t0
     nodes = s.interior_nodes()
     s.close()
+    b = 4 if fp32_io else 8
     return {"value": nodes * steps / el / 1e6, "unit": "MLUPS",
-            "h2d_bytes_per_step": int(8 * 10 * N / steps), "d2h_bytes_per_step": int(8 * 10 * N / steps),
-            "note": "init from pinned host FP64 moments + %d steps + moments back to pinned host, wall clock" % steps}
+            "h2d_bytes_per_step": int(b * 10 * N / steps), "d2h_bytes_per_step": int(b * 10 * N / steps),
+            "note": "init from pinned host %s moments + %d steps + moments back to pinned host, wall clock"
+                    % ("FP32 (tslb_init_moments_f32 / tslb_get_moments_f32)" if fp32_io else "FP64", steps)}
 
 
 def main():
@@ -530,9 +542,10 @@ def main():
             "value": job_mlups(nv, ws, args.steps, msv), "unit": "MLUPS",
             "roofline_frac": BYTES_PER_NODE["bf16"] * nv / (msv * 1e-3 / args.steps) / 1e9 / hbm,
             "bytes_per_node": BYTES_PER_NODE["bf16"], "stable": cv == T.TSLB_OK}
-    e2e = None
+    e2e = e2e64 = None
     if not args.no_e2e and rank == 0:
-        e2e = time_e2e(T, torch, prm, state, args.steps, stream)
+        e2e = time_e2e(T, torch, prm, state, args.steps, stream, fp32_io=True)
+        e2e64 = time_e2e(T, torch, prm, state, args.steps, stream, fp32_io=False)
     adj = None
     if not args.no_adjoint and rank == 0:
         adj = time_adjoint(T, torch, stream)
@@ -579,6 +592,7 @@ def main():
             "variants": variants,
             "precision_study": study,
             "e2e": e2e,
+            "e2e_fp64_io": e2e64,
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "adjoint": adj,

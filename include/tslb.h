@@ -192,6 +192,14 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
  * returns after the data are copied.  Resets the step counter to 0. */
 int tslb_init_moments(tslb_t* h, const double* rho, const double* u, const double* pi, int where);
 
+/* The same with FP32 arrays and the density given as its deviation drho = rho - 1
+ * (the stored quantity, so that FP32 keeps its precision): drho [N], u [3][N],
+ * pi [6][N] (may be NULL), full lattice, host or device per `where`.  With FP32
+ * storage a moment read back by tslb_get_moments_f32 is bit-identical to the
+ * value loaded.  Half the bytes of the FP64 form cross the host link.
+ * TSLB_D3Q27 only (TSLB_ERR_UNSUPPORTED otherwise). */
+int tslb_init_moments_f32(tslb_t* h, const float* drho, const float* u, const float* pi, int where);
+
 /* Per-node body-force acceleration F[3][N] (FP32, full lattice) replacing the
  * constant force; NULL restores the constant force given to tslb_create. */
 int tslb_set_force_field(tslb_t* h, const float* F, int where);
@@ -204,6 +212,10 @@ int tslb_step(tslb_t* h, int64_t nsteps);
 /* Copy the current moments out as full-lattice FP64 arrays (any pointer may
  * be NULL to skip that field).  Synchronises the handle's stream. */
 int tslb_get_moments(tslb_t* h, double* rho, double* u, double* pi, int where);
+
+/* The same into FP32 arrays, with the density as drho = rho - 1 (see
+ * tslb_init_moments_f32).  TSLB_D3Q27 only. */
+int tslb_get_moments_f32(tslb_t* h, float* drho, float* u, float* pi, int where);
 
 /* FP64 reductions over the interior nodes (mass, momentum, kinetic energy,
  * wall shear, max |u|, NaN/Inf count).  Synchronises the stream.  Returns

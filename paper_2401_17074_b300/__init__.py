@@ -90,9 +90,11 @@ def load(build_if_missing=True):
     L.tslb_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(i64), ctypes.c_double, dp,
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(tslb_options)]
     L.tslb_init_moments.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    L.tslb_init_moments_f32.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     L.tslb_set_force_field.argtypes = [vp, fp, ctypes.c_int]
     L.tslb_step.argtypes = [vp, i64]
     L.tslb_get_moments.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    L.tslb_get_moments_f32.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     L.tslb_diagnostics.argtypes = [vp, ctypes.POINTER(tslb_diag)]
     L.tslb_adjoint_force_gradient.argtypes = [vp, i64, fp, ctypes.c_int]
     L.tslb_interior_nodes.argtypes = [vp]
@@ -178,6 +180,26 @@ def tslb_set_force_field(h, F):
 
 def tslb_step(h, nsteps=1):
     _check(load().tslb_step(h, int(nsteps)), h)
+
+
+def tslb_init_moments_f32(h, drho, u, pi=None):
+    """FP32 moments with the density as drho = rho - 1 (numpy float32 or CUDA float32 tensors)."""
+    pr, w, k1 = _ptr(drho, np.float32)
+    pu, w2, k2 = _ptr(u, np.float32)
+    pp, w3, k3 = _ptr(pi, np.float32)
+    if pi is not None and not (w == w2 == w3):
+        raise ValueError("drho, u, pi must all be host or all device")
+    _check(load().tslb_init_moments_f32(h, pr, pu, pp, w), h)
+
+
+def tslb_get_moments_f32(h, drho=None, u=None, pi=None, where=HOST):
+    def p(a):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return ctypes.c_void_p(a.data_ptr())
+        return ctypes.c_void_p(a.ctypes.data)
+    _check(load().tslb_get_moments_f32(h, p(drho), p(u), p(pi), int(where)), h)
 
 
 def tslb_get_moments(h, rho=None, u=None, pi=None, where=HOST):
@@ -296,6 +318,18 @@ class Solver:
 
     def step(self, n=1):
         tslb_step(self._h, n)
+
+    def init_moments_f32(self, drho, u, pi=None):
+        """FP32 moments; the density given as drho = rho - 1 (tslb_init_moments_f32)."""
+        tslb_init_moments_f32(self._h, drho, u, pi)
+
+    def get_moments_f32(self):
+        """(drho, u, pi) as FP32 arrays, drho = rho - 1 (tslb_get_moments_f32)."""
+        drho = np.zeros(self.N, dtype=np.float32)
+        u = np.zeros(3 * self.N, dtype=np.float32)
+        pi = np.zeros(6 * self.N, dtype=np.float32)
+        tslb_get_moments_f32(self._h, drho, u, pi, HOST)
+        return drho, u.reshape(3, self.N), pi.reshape(6, self.N)
 
     def get_moments(self):
         rho = np.zeros(self.N)

@@ -157,6 +157,96 @@ void drop_checkpoints(tslb_s* h) { h->ckpt_valid = 0; }
 
 }  // namespace
 
+namespace tslb {
+cudaError_t launch_encode_f32(const tslb_s* h, const float* drho, const float* u, const float* pi, void* dst,
+                              const Physics& p);
+cudaError_t launch_decode_f32(const tslb_s* h, const void* src, float* drho, float* u, float* pi, const Physics& p);
+}  // namespace tslb
+
+namespace {
+
+// Host element type of the moment arrays: FP64 rho, or FP32 rho - 1.
+cudaError_t encode_any(const tslb_s* h, const double* r, const double* u, const double* pi, void* dst,
+                       const tslb::Physics& p) {
+    return tslb::launch_encode(h, r, u, pi, dst, p);
+}
+cudaError_t encode_any(const tslb_s* h, const float* r, const float* u, const float* pi, void* dst,
+                       const tslb::Physics& p) {
+    return tslb::launch_encode_f32(h, r, u, pi, dst, p);
+}
+cudaError_t decode_any(const tslb_s* h, const void* src, double* r, double* u, double* pi, const tslb::Physics& p) {
+    return tslb::launch_decode(h, src, r, u, pi, p);
+}
+cudaError_t decode_any(const tslb_s* h, const void* src, float* r, float* u, float* pi, const tslb::Physics& p) {
+    return tslb::launch_decode_f32(h, src, r, u, pi, p);
+}
+
+template <class H>
+int init_moments_impl(tslb_t* h, const H* rho, const H* u, const H* pi, int where) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (!rho || !u) return fail(h, TSLB_ERR_INVALID, "rho (or drho) and u are required");
+    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    cudaSetDevice(h->device);
+    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
+    const tslb::Physics p = tslb::make_physics(h);
+    cudaError_t e;
+    if (where == TSLB_DEVICE) {
+        e = encode_any(h, rho, u, pi, h->buf[h->cur], p);
+        if (e != cudaSuccess) return cuda_fail(h, e, "encode launch");
+    } else {
+        H* st = nullptr;
+        const size_t bytes = sizeof(H) * (size_t)fN * (pi ? 10 : 4);
+        e = dev_alloc_async((void**)&st, bytes, h->stream);
+        if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "staging allocation failed");
+        e = cudaMemcpyAsync(st, rho, sizeof(H) * fN, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(st + fN, u, sizeof(H) * 3 * fN, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess && pi)
+            e = cudaMemcpyAsync(st + 4 * fN, pi, sizeof(H) * 6 * fN, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = encode_any(h, st, st + fN, pi ? st + 4 * fN : nullptr, h->buf[h->cur], p);
+        cudaFreeAsync(st, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "init copy / encode");
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "init synchronize");
+    h->t = 0;
+    drop_checkpoints(h);
+    return TSLB_OK;
+}
+
+template <class H>
+int get_moments_impl(tslb_t* h, H* rho, H* u, H* pi, int where) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    cudaSetDevice(h->device);
+    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
+    const tslb::Physics p = tslb::make_physics(h);
+    cudaError_t e;
+    if (where == TSLB_DEVICE) {
+        e = decode_any(h, h->buf[h->cur], rho, u, pi, p);
+        if (e != cudaSuccess) return cuda_fail(h, e, "decode launch");
+    } else {
+        H* st = nullptr;
+        e = dev_alloc_async((void**)&st, sizeof(H) * (size_t)fN * 10, h->stream);
+        if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "staging allocation failed");
+        e = decode_any(h, h->buf[h->cur], rho ? st : nullptr, u ? st + fN : nullptr,
+                                pi ? st + 4 * fN : nullptr, p);
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(rho, st, sizeof(H) * fN, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && u)
+            e = cudaMemcpyAsync(u, st + fN, sizeof(H) * 3 * fN, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && pi)
+            e = cudaMemcpyAsync(pi, st + 4 * fN, sizeof(H) * 6 * fN, cudaMemcpyDeviceToHost, h->stream);
+        cudaFreeAsync(st, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get copy / decode");
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get synchronize");
+    return check_device_status(h);
+}
+
+}  // namespace
+
 extern "C" {
 
 int tslb_options_default(tslb_options* opt) {
@@ -360,35 +450,14 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
 
 int tslb_init_moments(tslb_t* h, const double* rho, const double* u, const double* pi, int where) {
     const Range range("tslb_init_moments");
-    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
-    if (!rho || !u) return fail(h, TSLB_ERR_INVALID, "rho and u are required");
-    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
-    cudaSetDevice(h->device);
-    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
-    const tslb::Physics p = tslb::make_physics(h);
-    cudaError_t e;
-    if (where == TSLB_DEVICE) {
-        e = tslb::launch_encode(h, rho, u, pi, h->buf[h->cur], p);
-        if (e != cudaSuccess) return cuda_fail(h, e, "encode launch");
-    } else {
-        double* st = nullptr;
-        const size_t bytes = sizeof(double) * (size_t)fN * (pi ? 10 : 4);
-        e = dev_alloc_async((void**)&st, bytes, h->stream);
-        if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "staging allocation failed");
-        e = cudaMemcpyAsync(st, rho, sizeof(double) * fN, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(st + fN, u, sizeof(double) * 3 * fN, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess && pi)
-            e = cudaMemcpyAsync(st + 4 * fN, pi, sizeof(double) * 6 * fN, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = tslb::launch_encode(h, st, st + fN, pi ? st + 4 * fN : nullptr, h->buf[h->cur], p);
-        cudaFreeAsync(st, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "init copy / encode");
-    }
-    e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "init synchronize");
-    h->t = 0;
-    drop_checkpoints(h);
-    return TSLB_OK;
+    return init_moments_impl<double>(h, rho, u, pi, where);
+}
+
+int tslb_init_moments_f32(tslb_t* h, const float* drho, const float* u, const float* pi, int where) {
+    const Range range("tslb_init_moments_f32");
+    if (valid_handle(h) && h->lattice != TSLB_D3Q27)
+        return fail(h, TSLB_ERR_UNSUPPORTED, "FP32 host moments are implemented for D3Q27");
+    return init_moments_impl<float>(h, drho, u, pi, where);
 }
 
 int tslb_set_force_field(tslb_t* h, const float* F, int where) {
@@ -465,33 +534,14 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
 
 int tslb_get_moments(tslb_t* h, double* rho, double* u, double* pi, int where) {
     const Range range("tslb_get_moments");
-    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
-    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
-    cudaSetDevice(h->device);
-    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
-    const tslb::Physics p = tslb::make_physics(h);
-    cudaError_t e;
-    if (where == TSLB_DEVICE) {
-        e = tslb::launch_decode(h, h->buf[h->cur], rho, u, pi, p);
-        if (e != cudaSuccess) return cuda_fail(h, e, "decode launch");
-    } else {
-        double* st = nullptr;
-        e = dev_alloc_async((void**)&st, sizeof(double) * (size_t)fN * 10, h->stream);
-        if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "staging allocation failed");
-        e = tslb::launch_decode(h, h->buf[h->cur], rho ? st : nullptr, u ? st + fN : nullptr,
-                                pi ? st + 4 * fN : nullptr, p);
-        if (e == cudaSuccess && rho)
-            e = cudaMemcpyAsync(rho, st, sizeof(double) * fN, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess && u)
-            e = cudaMemcpyAsync(u, st + fN, sizeof(double) * 3 * fN, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess && pi)
-            e = cudaMemcpyAsync(pi, st + 4 * fN, sizeof(double) * 6 * fN, cudaMemcpyDeviceToHost, h->stream);
-        cudaFreeAsync(st, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "get copy / decode");
-    }
-    e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "get synchronize");
-    return check_device_status(h);
+    return get_moments_impl<double>(h, rho, u, pi, where);
+}
+
+int tslb_get_moments_f32(tslb_t* h, float* drho, float* u, float* pi, int where) {
+    const Range range("tslb_get_moments_f32");
+    if (valid_handle(h) && h->lattice != TSLB_D3Q27)
+        return fail(h, TSLB_ERR_UNSUPPORTED, "FP32 host moments are implemented for D3Q27");
+    return get_moments_impl<float>(h, drho, u, pi, where);
 }
 
 int tslb_diagnostics(tslb_t* h, tslb_diag* out) {

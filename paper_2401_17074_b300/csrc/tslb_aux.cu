@@ -1,32 +1,33 @@
-// Moment codecs (FP64 <-> stored FP32 / BF16 / FP16 deviations) and the FP64
-// diagnostics reductions of the TSLB library.
+// Moment codecs (host FP64 or FP32 <-> stored FP32 / BF16 / FP16 deviations)
+// and the FP64 diagnostics reductions of the TSLB library.
 #include "tslb_internal.cuh"
 
 namespace tslb {
 namespace {
 
-// Full-lattice FP64 arrays -> interior storage (layout and 16-bit scaling in
-// NodeIO): rho - 1, u and Pi^neq.
-template <class Codec>
-__global__ void encode_kernel(const double* __restrict__ rho, const double* __restrict__ u,
-                              const double* __restrict__ pi, typename Codec::T* __restrict__ dst, Geometry g,
-                              long long fnx, long long fny, long long fN, Physics p) {
+// Full-lattice arrays -> interior storage (layout and 16-bit scaling in
+// NodeIO): rho - 1, u and Pi^neq.  H = double (rho given) or float (DEV: the
+// deviation rho - 1 given, as stored).
+template <class Codec, class H = double, bool DEV = false>
+__global__ void encode_kernel(const H* __restrict__ rho, const H* __restrict__ u, const H* __restrict__ pi,
+                              typename Codec::T* __restrict__ dst, Geometry g, long long fnx, long long fny,
+                              long long fN, Physics p) {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= g.plane * g.nz) return;
     const long long xi = n % g.nx, yi = (n / g.nx) % g.ny, zi = n / g.plane;
     const long long node = (xi + g.lo[0]) + fnx * ((yi + g.lo[1]) + fny * (zi + g.lo[2]));
     float v[NFIELDS];
-    v[F_DRHO] = (float)(rho[node] - 1.0);
+    v[F_DRHO] = DEV ? (float)rho[node] : (float)(rho[node] - 1.0);
     for (int a = 0; a < 3; ++a) v[F_UX + a] = (float)u[a * fN + node];
     for (int k = 0; k < 6; ++k) v[F_PXX + k] = pi ? (float)pi[k * fN + node] : 0.0f;
     NodeIO<Codec>::store(dst, g.fstride, n, p, v);
 }
 
-// Interior storage -> full-lattice FP64; boundary-layer nodes get the rest state.
-template <class Codec>
-__global__ void decode_kernel(const typename Codec::T* __restrict__ src, double* __restrict__ rho,
-                              double* __restrict__ u, double* __restrict__ pi, Geometry g, long long fnx,
-                              long long fny, long long fnz, Physics p) {
+// Interior storage -> full-lattice arrays (FP64 rho, or with DEV FP32 rho - 1);
+// boundary-layer nodes get the rest state.
+template <class Codec, class H = double, bool DEV = false>
+__global__ void decode_kernel(const typename Codec::T* __restrict__ src, H* __restrict__ rho, H* __restrict__ u,
+                              H* __restrict__ pi, Geometry g, long long fnx, long long fny, long long fnz, Physics p) {
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long fN = fnx * fny * fnz;
     if (node >= fN) return;
@@ -39,11 +40,11 @@ __global__ void decode_kernel(const typename Codec::T* __restrict__ src, double*
     } else {
         for (int f = 0; f < NFIELDS; ++f) v[f] = 0.0f;
     }
-    if (rho) rho[node] = 1.0 + (double)v[F_DRHO];
+    if (rho) rho[node] = DEV ? (H)v[F_DRHO] : (H)(1.0 + (double)v[F_DRHO]);
     if (u)
-        for (int a = 0; a < 3; ++a) u[a * fN + node] = (double)v[F_UX + a];
+        for (int a = 0; a < 3; ++a) u[a * fN + node] = (H)v[F_UX + a];
     if (pi)
-        for (int k = 0; k < 6; ++k) pi[k * fN + node] = (double)v[F_PXX + k];
+        for (int k = 0; k < 6; ++k) pi[k * fN + node] = (H)v[F_PXX + k];
 }
 
 // FP64 block reduction of [mass, jx, jy, jz, ke, shear_sum, max_speed, nonfinite].
@@ -151,6 +152,51 @@ cudaError_t launch_decode(const tslb_s* h, const void* src, double* rho, double*
         default:
             decode_kernel<CodecF16><<<blocks, threads, 0, h->stream>>>((const __half*)src, rho, u, pi, h->g,
                                                                        h->dims[0], h->dims[1], h->dims[2], p);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+// FP32 host interface (D3Q27): drho = rho - 1, u and Pi^neq as FP32 full-lattice arrays.
+cudaError_t launch_encode_f32(const tslb_s* h, const float* drho, const float* u, const float* pi, void* dst,
+                              const Physics& p) {
+    const long long total = h->g.plane * h->g.nz;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((total + threads - 1) / threads);
+    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
+    switch (h->precision) {
+        case TSLB_FP32:
+            encode_kernel<CodecF32, float, true><<<blocks, threads, 0, h->stream>>>(drho, u, pi, (float*)dst, h->g,
+                                                                                   h->dims[0], h->dims[1], fN, p);
+            break;
+        case TSLB_BF16:
+            encode_kernel<CodecBF16, float, true><<<blocks, threads, 0, h->stream>>>(
+                drho, u, pi, (__nv_bfloat16*)dst, h->g, h->dims[0], h->dims[1], fN, p);
+            break;
+        default:
+            encode_kernel<CodecF16, float, true><<<blocks, threads, 0, h->stream>>>(drho, u, pi, (__half*)dst, h->g,
+                                                                                   h->dims[0], h->dims[1], fN, p);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_f32(const tslb_s* h, const void* src, float* drho, float* u, float* pi, const Physics& p) {
+    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((fN + threads - 1) / threads);
+    switch (h->precision) {
+        case TSLB_FP32:
+            decode_kernel<CodecF32, float, true><<<blocks, threads, 0, h->stream>>>(
+                (const float*)src, drho, u, pi, h->g, h->dims[0], h->dims[1], h->dims[2], p);
+            break;
+        case TSLB_BF16:
+            decode_kernel<CodecBF16, float, true><<<blocks, threads, 0, h->stream>>>(
+                (const __nv_bfloat16*)src, drho, u, pi, h->g, h->dims[0], h->dims[1], h->dims[2], p);
+            break;
+        default:
+            decode_kernel<CodecF16, float, true><<<blocks, threads, 0, h->stream>>>(
+                (const __half*)src, drho, u, pi, h->g, h->dims[0], h->dims[1], h->dims[2], p);
             break;
     }
     return cudaGetLastError();
