@@ -12,6 +12,9 @@ import math
 import numpy as np
 import pytest
 
+from hypothesis import HealthCheck, given, settings
+from hypothesis import strategies as st
+
 import oracle
 import paper_2401_17074_b300 as T
 from paper_2401_17074_b300 import workloads as W
@@ -119,3 +122,19 @@ def test_d2q9_rejections(cuda_ok):
         s.set_force_field(np.zeros((3, 128), np.float32))
     assert ei.value.code == T.TSLB_ERR_UNSUPPORTED
     s.close()
+
+
+
+@settings(max_examples=60, deadline=None,
+          suppress_health_check=[HealthCheck.too_slow, HealthCheck.function_scoped_fixture])
+@given(nx=st.integers(3, 100), ny=st.integers(4, 300), walls=st.booleans(), tau=st.floats(0.55, 1.5),
+       seed=st.integers(0, 10 ** 6), F=st.tuples(st.floats(-2e-5, 2e-5), st.floats(-2e-5, 2e-5)))
+def test_random_boxes_two_steps(cuda_ok, nx, ny, walls, tau, seed, F):
+    """Random box sizes (ragged against the 30-column warps and the y chunks of
+    the one-wave grid), periodic or bounce-back y faces, tau, force and seed:
+    two steps from random moments within 4e-6 per field (twice the one-step
+    bound)."""
+    dims = (nx, ny, 1)
+    bc = (0, 0, 1, 1, 0, 0) if walls else (0,) * 6
+    errs = _run(dims, tau, _random3(dims, seed), 2, bc=bc, force=(F[0], F[1], 0.0))
+    assert max(errs.values()) <= 4e-6, (errs, dims, walls, tau)
