@@ -203,6 +203,21 @@ def cpu_baseline(prm, seconds, nz_sample=None):
                       % (nx, ny, nz_s, steps, el)}
 
 
+def cpu_single_core(prm, seconds):
+    """The same oracle timing on one host core: a child process with
+    OMP_NUM_THREADS=1 (a separate process, so the thread count is set before the
+    OpenMP runtime starts), on a 3-plane slab."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_baseline(%r, %r, nz_sample=3)))" % (ROOT, {"dims": prm["dims"]}, seconds))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                       timeout=max(120, 10 * seconds))
+    if r.returncode != 0:
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": d["unit"], "cores": 1, "sample": d["sample"]}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -603,6 +618,7 @@ def main():
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(prm, args.cpu_seconds)
+        cpu["single_core"] = cpu_single_core(prm, min(5.0, args.cpu_seconds))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
