@@ -203,6 +203,38 @@ def cpu_baseline(prm, seconds, nz_sample=None):
                       % (nx, ny, nz_s, steps, el)}
 
 
+def cpu_other_configs(seconds):
+    """The oracle, as it stands, on the other workloads' set-ups (all host cores,
+    bounded samples): the 32^3 Taylor-Green vortex in full, and a 10-layer slab
+    of the 256 x 256 x 640 jet (inflow and outflow faces, free-slip sides)."""
+    import oracle
+    from paper_2401_17074_b300 import workloads as W
+
+    def timed(sim, nodes):
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            sim.step(1)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds or steps >= 200:
+                return nodes * steps / el / 1e6, steps, el
+
+    out = {}
+    dims, state = W.taylor_green(n=32, u0=0.05, tau=0.6)
+    s = oracle.OracleSim(dims, 0.6)
+    s.init_moments(*state)
+    v, n, el = timed(s, 32 ** 3)
+    out["taylor_green_32"] = {"value": v, "unit": "MLUPS", "sample": "32^3, %d steps, %.1f s" % (n, el)}
+    prm = W.jet_params(nz=10)
+    s = oracle.OracleSim(prm["dims"], prm["tau"], bc=prm["bc"], inflow=prm["inflow"])
+    s.init_moments(*W.rest_state(prm["dims"]))
+    v, n, el = timed(s, 254 * 254 * 8)
+    out["jet_slab"] = {"value": v, "unit": "MLUPS",
+                       "sample": "256x256x10 slab of the jet (inflow, outflow, free-slip), %d steps, %.1f s" % (n, el)}
+    return out
+
+
 def cpu_single_core(prm, seconds):
     """The same oracle timing on one host core: a child process with
     OMP_NUM_THREADS=1 (a separate process, so the thread count is set before the
@@ -619,6 +651,7 @@ def main():
     if not args.no_cpu and rank == 0 and ws == 1:
         cpu = cpu_baseline(prm, args.cpu_seconds)
         cpu["single_core"] = cpu_single_core(prm, min(5.0, args.cpu_seconds))
+        cpu["other_configs"] = cpu_other_configs(min(3.0, args.cpu_seconds))
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
