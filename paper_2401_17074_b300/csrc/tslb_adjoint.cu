@@ -95,8 +95,9 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
                                                  float* __restrict__ gbar_out, float* __restrict__ fbar, Geometry g,
                                                  Physics p) {
     // The block's AX x AY x AZ nodes and a one-node halo of Gbar, all ten
-    // fields, staged in shared memory with periodic wrap; the 27 directions
-    // then read it at constant offsets from the thread's cell.
+    // fields, staged in shared memory with periodic wrap (cp.async copies, all
+    // of a thread's in flight at once, no register round trip); the 27
+    // directions then read it at constant offsets from the thread's cell.
     __shared__ float tile[NFIELDS * HC];
     const int tx = threadIdx.x % AX, ty = (threadIdx.x / AX) % AY, tz = threadIdx.x / (AX * AY);
     const int ox = (int)blockIdx.x * AX, oy = (int)blockIdx.y * AY, oz = (int)blockIdx.z * AZ;  // block origin
@@ -116,8 +117,16 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
             const float* G = gbar + gi;
             const bool ok = TSLB_IN_RANGE(gi, g.plane * g.nz, p.err);
 #pragma unroll
-            for (int f = 0; f < NFIELDS; ++f) tile[f * HC + c] = ok ? __ldg(G + f * fs) : 0.0f;
+            for (int f = 0; f < NFIELDS; ++f) {
+                if (ok) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&tile[f * HC + c]);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(G + f * fs) : "memory");
+                } else {
+                    tile[f * HC + c] = 0.0f;
+                }
+            }
         }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
     const int px = ox + tx, py = oy + ty, pz = oz + tz;  // this thread's source node
@@ -125,8 +134,7 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     const long long n = (long long)px + (long long)g.nx * py + g.plane * (long long)pz;
     const float* Tc = tile + (tz + 1) * (HX * HY) + (ty + 1) * HX + (tx + 1);
     float Ab[NMODES];
-#pragma unroll
-    for (int k = 0; k < NMODES; ++k) Ab[k] = 0.0f;
+    float gbv[3][3][3];  // adjoint populations gb(c), [cz + 1][cy + 1][cx + 1]
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz)
 #pragma unroll
@@ -145,15 +153,38 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
                 if (cx != 0 && cy != 0) gb = fmaf((float)(cx * cy), G[7 * HC], gb);
                 if (cx != 0 && cz != 0) gb = fmaf((float)(cx * cz), G[8 * HC], gb);
                 if (cy != 0 && cz != 0) gb = fmaf((float)(cy * cz), G[9 * HC], gb);
-                const float w = wgt(cx) * wgt(cy) * wgt(cz);
-#pragma unroll
-                for (int k = 0; k < NMODES; ++k) {
-                    int k1, k2, k3;
-                    mode_digits(k, k1, k2, k3);
-                    const float c = w * phi(k1, cx) * phi(k2, cy) * phi(k3, cz);
-                    if (c != 0.0f) Ab[k] = fmaf(c, gb, Ab[k]);
-                }
+                gbv[cz + 1][cy + 1][cx + 1] = gb;
             }
+    // Modes of the adjoint populations, Ab_k = sum_c w(c) phi_k(c) gb(c), one
+    // axis at a time: the 1-D weights w phi_0, w phi_1, w phi_2 over c = -1, 0, 1
+    // are (1, 4, 1), (-1, 0, 1) and (2, -4, 2).
+    float T1[3][3][3];  // [kx][cz][cy]
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            const float a = gbv[z][y][0], b = gbv[z][y][1], c = gbv[z][y][2], e = a + c;
+            T1[0][z][y] = fmaf(4.0f, b, e);
+            T1[1][z][y] = c - a;
+            T1[2][z][y] = fmaf(-4.0f, b, 2.0f * e);
+        }
+    float T2[3][3][3];  // [kx][ky][cz]
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+        for (int z = 0; z < 3; ++z) {
+            const float a = T1[kx][z][0], b = T1[kx][z][1], c = T1[kx][z][2], e = a + c;
+            T2[kx][0][z] = fmaf(4.0f, b, e);
+            T2[kx][1][z] = c - a;
+            T2[kx][2][z] = fmaf(-4.0f, b, 2.0f * e);
+        }
+#pragma unroll
+    for (int k = 0; k < NMODES; ++k) {
+        int k1, k2, k3;
+        mode_digits(k, k1, k2, k3);
+        const float a = T2[k1][k2][0], b = T2[k1][k2][1], c = T2[k1][k2][2];
+        Ab[k] = k3 == 0 ? fmaf(4.0f, b, a + c) : (k3 == 1 ? c - a : fmaf(-4.0f, b, 2.0f * (a + c)));
+    }
     // transpose of post_modes (u = v, constant or per-node force)
     float m[NFIELDS];
     load_m<Codec>(m_cur, g.fstride, n, p, m);
