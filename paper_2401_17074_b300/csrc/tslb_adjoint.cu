@@ -79,8 +79,15 @@ __global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __r
 }
 
 // Gather blocks: AX x AY x AZ nodes (x fastest), halo tile HX x HY x HZ.
+// A tile row holds its HX cells at XOFF .. XOFF + HX - 1 of a PX-float pitch,
+// so the AX block columns start on a 16-byte boundary.
 constexpr int AX = 32, AY = 4, AZ = 2, AT = AX * AY * AZ;
-constexpr int HX = AX + 2, HY = AY + 2, HZ = AZ + 2, HC = HX * HY * HZ;
+constexpr int HX = AX + 2, HY = AY + 2, HZ = AZ + 2;
+constexpr int PX = 40, XOFF = 3, HC = PX * HY * HZ;
+// Row copies of the 16-byte tile load: AX / 4 vector pieces and two halo cells.
+constexpr int PIECES = AX / 4 + 2;
+static_assert(HY * HZ * PIECES <= AT, "one row piece per thread");
+static_assert((XOFF + 1) % 4 == 0 && PX % 4 == 0 && XOFF + HX <= PX, "aligned block columns");
 
 // Transpose gather + transpose of post_modes at the source node y, then the
 // Gbar of the preceding step at y (gbar_in belongs to the step m_cur -> m_next,
@@ -89,7 +96,10 @@ constexpr int HX = AX + 2, HY = AY + 2, HZ = AZ + 2, HC = HX * HY * HZ;
 // a direction loads only the moment sums whose monomial psi_t(c) is nonzero
 // (1, 3, 6 or 10 of them for c with 0, 1, 2 or 3 nonzero components), and
 // adds only to the modes whose weight w(c) phi_k(c) is nonzero (phi_1(0) = 0).
-template <class Codec>
+// VEC: nx is a multiple of 4 and at least AX, so a block's columns, wrapped
+// once, are whole aligned groups of 4 and each tile row is AX / 4 16-byte
+// copies plus its two halo cells.
+template <class Codec, bool VEC>
 __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
                                                  const typename Codec::T* __restrict__ m_cur,
                                                  float* __restrict__ gbar_out, float* __restrict__ fbar, Geometry g,
@@ -98,16 +108,46 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     // fields, staged in shared memory with periodic wrap (cp.async copies, all
     // of a thread's in flight at once, no register round trip); the 27
     // directions then read it at constant offsets from the thread's cell.
-    __shared__ float tile[NFIELDS * HC];
+    __shared__ __align__(16) float tile[NFIELDS * HC];
     const int tx = threadIdx.x % AX, ty = (threadIdx.x / AX) % AY, tz = threadIdx.x / (AX * AY);
     const int ox = (int)blockIdx.x * AX, oy = (int)blockIdx.y * AY, oz = (int)blockIdx.z * AZ;  // block origin
     const long long fs = g.fstride;
-    {
+    const unsigned total = (unsigned)(g.plane * g.nz);
+    if (VEC) {
+        // thread t copies piece t % PIECES of tile row t / PIECES, all ten fields
+        const int t = threadIdx.x;
+        if (t < HY * HZ * PIECES) {
+            const int row = t / PIECES, s = t - row * PIECES;
+            const int hy = row % HY, hz = row / HY;
+            int gy = oy - 1 + hy, gz = oz - 1 + hz;
+            gy = gy < 0 ? gy + g.ny : (gy >= g.ny ? gy - g.ny : gy);
+            gz = gz < 0 ? gz + g.nz : (gz >= g.nz ? gz - g.nz : gz);
+            // halo cells first (s = 0: x = ox - 1, s = 1: x = ox + AX), then
+            // the 16-byte pieces of columns ox + 4 (s - 2) ...
+            int hx = s == 0 ? 0 : (s == 1 ? HX - 1 : 1 + 4 * (s - 2));
+            int gx = ox - 1 + hx;
+            gx = gx < 0 ? gx + g.nx : (gx >= g.nx ? gx - g.nx : gx);
+            const unsigned gi = (unsigned)gx + (unsigned)g.nx * (unsigned)gy + (unsigned)g.plane * (unsigned)gz;
+            const float* G = gbar + gi;
+            unsigned dst = (unsigned)__cvta_generic_to_shared(&tile[(hz * HY + hy) * PX + XOFF + hx]);
+            if (s >= 2) {
+                if (TSLB_IN_RANGE(gi + 3, total, p.err)) {
+#pragma unroll
+                    for (int f = 0; f < NFIELDS; ++f, dst += 4 * HC)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(G + f * fs) : "memory");
+                }
+            } else if (TSLB_IN_RANGE(gi, total, p.err)) {
+#pragma unroll
+                for (int f = 0; f < NFIELDS; ++f, dst += 4 * HC)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(G + f * fs) : "memory");
+            }
+        }
+    } else {
         // one-step wrap holds for coordinates in [-n, 2n): always in y and z
         // (periodic axes of at least 3 nodes), in x unless the lattice is
         // narrower than about half a block
         const bool xwrap1 = ox + AX < 2 * g.nx;
-        for (int c = threadIdx.x; c < HC; c += AT) {
+        for (int c = threadIdx.x; c < HX * HY * HZ; c += AT) {
             const int hx = c % HX, hy = (c / HX) % HY, hz = c / (HX * HY);
             int gx = ox - 1 + hx, gy = oy - 1 + hy, gz = oz - 1 + hz;
             gx = xwrap1 ? (gx < 0 ? gx + g.nx : (gx >= g.nx ? gx - g.nx : gx)) : ((gx % g.nx) + g.nx) % g.nx;
@@ -115,24 +155,37 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
             gz = gz < 0 ? gz + g.nz : (gz >= g.nz ? gz - g.nz : gz);
             const unsigned gi = (unsigned)gx + (unsigned)g.nx * (unsigned)gy + (unsigned)g.plane * (unsigned)gz;
             const float* G = gbar + gi;
-            const bool ok = TSLB_IN_RANGE(gi, g.plane * g.nz, p.err);
+            const bool ok = TSLB_IN_RANGE(gi, total, p.err);
+            float* T = &tile[(hz * HY + hy) * PX + XOFF + hx];
 #pragma unroll
             for (int f = 0; f < NFIELDS; ++f) {
                 if (ok) {
-                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&tile[f * HC + c]);
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(T + f * HC);
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(G + f * fs) : "memory");
                 } else {
-                    tile[f * HC + c] = 0.0f;
+                    T[f * HC] = 0.0f;
                 }
             }
         }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
     }
-    __syncthreads();
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // the node's own state and force load while the tile copies are in flight
     const int px = ox + tx, py = oy + ty, pz = oz + tz;  // this thread's source node
-    if (px >= g.nx || py >= g.ny || pz >= g.nz) return;
-    const long long n = (long long)px + (long long)g.nx * py + g.plane * (long long)pz;
-    const float* Tc = tile + (tz + 1) * (HX * HY) + (ty + 1) * HX + (tx + 1);
+    const bool active = px < g.nx && py < g.ny && pz < g.nz;
+    const long long n = active ? (long long)px + (long long)g.nx * py + g.plane * (long long)pz : 0;
+    float m[NFIELDS];
+    load_m<Codec>(m_cur, g.fstride, n, p, m);
+    float F[3] = {p.F[0], p.F[1], p.F[2]};
+    if (p.force) {
+        F[0] = p.force[n];
+        F[1] = p.force[g.fstride + n];
+        F[2] = p.force[2 * g.fstride + n];
+    }
+    const float fb_old[3] = {fbar[n], fbar[fs + n], fbar[2 * fs + n]};
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (!active) return;
+    const float* Tc = tile + (tz + 1) * (PX * HY) + (ty + 1) * PX + XOFF + (tx + 1);
     float Ab[NMODES];
     float gbv[3][3][3];  // adjoint populations gb(c), [cz + 1][cy + 1][cx + 1]
 #pragma unroll
@@ -141,7 +194,7 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
         for (int cy = -1; cy <= 1; ++cy)
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
-                const float* G = Tc + cz * (HX * HY) + cy * HX + cx;
+                const float* G = Tc + cz * (PX * HY) + cy * PX + cx;
                 // adjoint population: psi(c) . Gbar(y + c), nonzero terms only
                 float gb = G[0];
                 if (cx != 0) gb = fmaf((float)cx, G[1 * HC], gb);
@@ -186,14 +239,6 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
         Ab[k] = k3 == 0 ? fmaf(4.0f, b, a + c) : (k3 == 1 ? c - a : fmaf(-4.0f, b, 2.0f * (a + c)));
     }
     // transpose of post_modes (u = v, constant or per-node force)
-    float m[NFIELDS];
-    load_m<Codec>(m_cur, g.fstride, n, p, m);
-    float F[3] = {p.F[0], p.F[1], p.F[2]};
-    if (p.force) {
-        F[0] = p.force[n];
-        F[1] = p.force[g.fstride + n];
-        F[2] = p.force[2 * g.fstride + n];
-    }
     const float w1 = p.omega1;
     const float rho = 1.0f + m[F_DRHO];
     const float u[3] = {m[F_UX], m[F_UY], m[F_UZ]};
@@ -273,9 +318,9 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     finish_transpose(m, l, gb);
 #pragma unroll
     for (int f = 0; f < NFIELDS; ++f) gbar_out[f * fs + n] = gb[f];
-    fbar[n] += fb[0];
-    fbar[fs + n] += fb[1];
-    fbar[2 * fs + n] += fb[2];
+    fbar[n] = fb_old[0] + fb[0];
+    fbar[fs + n] = fb_old[1] + fb[1];
+    fbar[2 * fs + n] = fb_old[2] + fb[2];
 }
 
 template <class Codec>
@@ -288,7 +333,10 @@ cudaError_t adj_launch_all(const tslb_s* h, int which, const void* a, const void
     else {
         const dim3 grid((unsigned)((h->g.nx + AX - 1) / AX), (unsigned)((h->g.ny + AY - 1) / AY),
                         (unsigned)((h->g.nz + AZ - 1) / AZ));
-        adj_gather<Codec><<<grid, AT, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
+        if (h->g.nx % 4 == 0 && h->g.nx >= AX)
+            adj_gather<Codec, true><<<grid, AT, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
+        else
+            adj_gather<Codec, false><<<grid, AT, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
     }
     return cudaGetLastError();
 }

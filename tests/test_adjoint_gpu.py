@@ -96,11 +96,14 @@ def test_adjoint_matches_complex_step_128(cuda_ok):
     assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (d_adj, d_cs)
 
 
-def test_adjoint_ragged_box_with_force(cuda_ok):
-    """A box that the gather's 32 x 4 x 2 blocks do not tile (70 x 9 x 5: ragged
-    blocks on every axis, x wider than a block, so the halo wraps in one step),
-    a nonzero random force field, and checkpoint segments of 8, 8 and 4 steps."""
-    dims, tau, nsteps = (70, 9, 5), 0.55, 20
+@pytest.mark.parametrize("dims", [(70, 9, 5), (68, 7, 5)], ids=["cell-copies", "row-copies"])
+def test_adjoint_ragged_box_with_force(cuda_ok, dims):
+    """Boxes that the gather's 32 x 4 x 2 blocks do not tile (ragged blocks on
+    every axis, x wider than a block, so the halo wraps in one step), a nonzero
+    random force field, and checkpoint segments of 8, 8 and 4 steps.  70 x 9 x 5
+    takes the per-cell tile load; 68 x 7 x 5 (nx a multiple of 4) the 16-byte
+    row copies, whose last block's columns wrap to x = 0."""
+    tau, nsteps = 0.55, 20
     N = dims[0] * dims[1] * dims[2]
     state = W.random_state(dims, seed=38, drho=0.002, du=0.02, dpi=1e-4)
     F0 = (1e-5 * np.random.default_rng(39).uniform(-1, 1, (3, N))).astype(np.float32)
