@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     const int tx = threadIdx.x % AX, ty = (threadIdx.x / AX) % AY, tz = threadIdx.x / (AX * AY);
     const int ox = (int)blockIdx.x * AX, oy = (int)blockIdx.y * AY, oz = (int)blockIdx.z * AZ;  // block origin
     const long long fs = g.fstride;
-    const unsigned total = (unsigned)(g.plane * g.nz);
+    [[maybe_unused]] const unsigned total = (unsigned)(g.plane * g.nz);
     if (VEC) {
         // thread t copies piece t % PIECES of tile row t / PIECES, all ten fields
         const int t = threadIdx.x;

@@ -78,8 +78,14 @@ constexpr int NCORR = 8;
 constexpr size_t CORRBUF = sizeof(float) * 2 * 2 * NCORR * 32;
 // Exchange mbarriers: [WROWS rows][2 buffers].
 constexpr size_t BARBUF = sizeof(uint64_t) * WROWS * 2;
-template <int E>
-constexpr size_t smem_bytes() { return 2 * YBUF + 2 * Prefetch<E>::BUF + CORRBUF + BARBUF; }
+// With a force field: [2 buffers][NT threads] slots of the node's three force
+// components (16 bytes each), prefetched with the moments.
+constexpr size_t FSLOT = 16;
+constexpr size_t FBUF = FSLOT * NT;
+template <int E, bool FORCE>
+constexpr size_t smem_bytes() {
+    return 2 * YBUF + 2 * Prefetch<E>::BUF + CORRBUF + BARBUF + (FORCE ? 2 * FBUF : 0);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 template <int BYTES>
@@ -340,7 +346,7 @@ struct Ctx {
 #endif
 };
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE>
 struct Kernel {
     typedef typename Codec::T T;
     static constexpr bool HOIST = sizeof(T) != 4;
@@ -349,26 +355,47 @@ struct Kernel {
     // zs-2 on entry and p+ of plane zs on exit; cOld holds c of zs-1; cNew
     // receives c of zs.
     typedef Prefetch<(int)sizeof(T)> PF;
+    // FORCE: the force slots of buffer PAR, after the mbarriers
+    static constexpr size_t FOFF = 2 * PF::BUF + CORRBUF + BARBUF;
 
     // Start the copies of stored plane zl's moments (march plane j, PAR = j & 1)
     // into prefetch buffer PAR.
     template <int PAR>
-    static __device__ __forceinline__ void prefetch_plane(const Ctx& c, const Geometry& g, const T* __restrict__ src,
-                                                          char* pfb, int zl) {
+    static __device__ __forceinline__ void prefetch_plane(const Ctx& c, const Geometry& g, const Physics& p,
+                                                          const T* __restrict__ src, char* pfb, int zl) {
         const unsigned n = c.col + c.plane * (unsigned)zl;
         char* b = pfb + PAR * PF::BUF;
         if (TSLB_IN_RANGE(n, g.plane * g.nz, c.err)) {
             cp_async<PF::B01>(smem_u32(b + c.tid * PF::B01), src + (size_t)n * 4);
             cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * g.fstride + (size_t)n * 4);
             cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * g.fstride + (size_t)n * 2);
+            if (FORCE) {
+                const uint32_t f = smem_u32(pfb + FOFF + PAR * FBUF + c.tid * FSLOT);
+                cp_async<4>(f, p.force + n);
+                cp_async<4>(f + 4, p.force + g.fstride + n);
+                cp_async<4>(f + 8, p.force + 2 * g.fstride + n);
+            }
         }
         cp_async_commit();
     }
     template <int PAR>
-    static __device__ __forceinline__ void prefetch(const Ctx& c, const Geometry& g, const T* __restrict__ src,
-                                                    char* pfb, int j) {
+    static __device__ __forceinline__ void prefetch(const Ctx& c, const Geometry& g, const Physics& p,
+                                                    const T* __restrict__ src, char* pfb, int j) {
         bool ig;
-        prefetch_plane<PAR>(c, g, src, pfb, plane_of(c.z0 - 1 + j, g, c.zper, ig));
+        prefetch_plane<PAR>(c, g, p, src, pfb, plane_of(c.z0 - 1 + j, g, c.zper, ig));
+    }
+    // Body force of the node in prefetch buffer PAR (stored index idx).
+    template <int PAR>
+    static __device__ __forceinline__ void node_force(const Ctx& c, const Geometry& g, const Physics& p,
+                                                      const char* pfb, unsigned idx, float& F0, float& F1, float& F2) {
+        if (FORCE) {
+            const float* f = reinterpret_cast<const float*>(pfb + FOFF + PAR * FBUF + c.tid * FSLOT);
+            F0 = f[0];
+            F1 = f[1];
+            F2 = f[2];
+        } else {
+            load_force(p, g, idx, F0, F1, F2);
+        }
     }
 
     // STEADY: 2 <= j <= np - 3, so the plane and the next one are stored
@@ -390,8 +417,8 @@ struct Kernel {
                                 ? __ldg(p.omega1_z + zfull) * p.s_pi
                                 : p.omega1_pi;
         // next plane's copies go out before this plane's are consumed
-        if (STEADY) prefetch_plane<PAR ^ 1>(c, g, src, pfb, zs + 1);
-        else if (zs < c.z1) prefetch<PAR ^ 1>(c, g, src, pfb, j + 1);
+        if (STEADY) prefetch_plane<PAR ^ 1>(c, g, p, src, pfb, zs + 1);
+        else if (zs < c.z1) prefetch<PAR ^ 1>(c, g, p, src, pfb, j + 1);
         else cp_async_commit();
         cp_async_wait_prev();
         const char* pb = pfb + PAR * PF::BUF;
@@ -416,7 +443,7 @@ struct Kernel {
                                      om_pi));
             } else {
                 float F0, F1, F2;
-                load_force(p, g, idx, F0, F1, F2);
+                node_force<PAR>(c, g, p, pfb, idx, F0, F1, F2);
                 h = hermite_p<GUO>(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2, om_pi);
             }
             zpops(h, P);
@@ -571,7 +598,7 @@ struct Kernel {
             float m[NFIELDS];
             NodeIO<Codec>::decode_smem_rawpi(v0, v1, v2, p, m);
             float F0, F1, F2;
-            load_force(p, g, idx, F0, F1, F2);
+            node_force<PAR>(c, g, p, pfb, idx, F0, F1, F2);
             bounce_back_correction(m, F0, F1, F2, om_pi, c.y < 0 ? 1.0f : -1.0f,
                                    corr + ((PAR * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
         }
@@ -618,12 +645,14 @@ struct Kernel {
     }
 };
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE>
 __global__ void __launch_bounds__(NT, 1)
     step_factored_kernel(const typename Codec::T* __restrict__ src, typename Codec::T* __restrict__ dst, Geometry g,
                          Physics p, int zchunk) {
-    typedef Kernel<Codec, XFREE, SPONGE, NEEY, GUO> K;
-    extern __shared__ __align__(16) float ysm[];  // [2][YBUF] y exchange, then [2][PF::BUF] plane prefetch
+    typedef Kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE> K;
+    // [2][YBUF] y exchange, [2][PF::BUF] plane prefetch, corrections, mbarriers,
+    // and with FORCE [2][FBUF] force slots
+    extern __shared__ __align__(16) float ysm[];
     char* pfb = reinterpret_cast<char*>(ysm) + 2 * YBUF;
     float* corr = reinterpret_cast<float*>(pfb + 2 * K::PF::BUF);
     uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(corr) + CORRBUF);
@@ -690,7 +719,7 @@ __global__ void __launch_bounds__(NT, 1)
     c.z1 = min(c.z0 + zchunk, g.nz);
     c.np = c.z1 - c.z0 + 2;
 
-    K::template prefetch<0>(c, g, src, pfb, 0);
+    K::template prefetch<0>(c, g, p, src, pfb, 0);
     f2 ppA[4], ppB[4], cA[4], cB[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) ppA[i] = ppB[i] = cA[i] = cB[i] = k2(0.0f);
@@ -711,13 +740,13 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE = false>
 cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY, GUO>;
+    auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE>;
     static bool configured[64] = {};
     const int dev = h->device;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    constexpr size_t SMEM = smem_bytes<(int)sizeof(typename Codec::T)>();
+    constexpr size_t SMEM = smem_bytes<(int)sizeof(typename Codec::T), FORCE>();
     if (!configured[dev]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e != cudaSuccess) return e;
@@ -761,8 +790,10 @@ cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Phys
     if (xfree)
         return sponge ? launch_t<Codec, true, true, false, false>(h, src, dst, p)
                       : launch_t<Codec, true, false, false, false>(h, src, dst, p);
-    return sponge ? launch_t<Codec, false, true, false, false>(h, src, dst, p)
-                  : launch_t<Codec, false, false, false, false>(h, src, dst, p);
+    if (sponge) return launch_t<Codec, false, true, false, false>(h, src, dst, p);
+    // a force field: its components prefetched with the moments
+    return p.force ? launch_t<Codec, false, false, false, false, true>(h, src, dst, p)
+                   : launch_t<Codec, false, false, false, false>(h, src, dst, p);
 }
 
 }  // namespace

@@ -282,6 +282,23 @@ def test_force_field(cuda_ok, kernel):
     assert_all_below(errs, 3e-6)
 
 
+@pytest.mark.parametrize("case", [("periodic", T.FP32, 3e-6), ("walls", T.FP32, 3e-6), ("walls", T.BF16, 2e-2)],
+                         ids=["periodic-fp32", "bounce-back-fp32", "bounce-back-bf16"])
+def test_force_field_multi_tile(cuda_ok, case):
+    """A per-node force field on a box of several tiles with ragged tails in x
+    and y and several z chunks, so the factored kernel's prefetched force
+    components are used in its steady loop, at chunk ends and, with walls, in
+    the bounce-back correction of the ghost rows."""
+    walls, prec, tol = case
+    dims = (70, 20, 40)
+    bc = (0, 0, 1, 1, 0, 0) if walls == "walls" else (0,) * 6
+    N = dims[0] * dims[1] * dims[2]
+    state = W.random_state(dims, seed=28, drho=0.002, du=0.02, dpi=1e-4)
+    F = (1e-4 * np.random.default_rng(29).standard_normal((3, N))).astype(np.float32)
+    errs, _, _ = run_pair(dims, 0.6, state, 6, T.KERNEL_FACTORED, bc=bc, force_field=F, precision=prec)
+    assert_all_below(errs, tol)
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_rest_state_is_exact(cuda_ok, kernel):
     dims = (9, 10, 11)
