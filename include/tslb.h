@@ -26,7 +26,12 @@
  *     xx, yy, zz, xy, xz, yz.  Boundary-layer entries are ignored on input
  *     and returned as the rest state (rho = 1, u = 0, Pi = 0) on output.
  *   - `where` says whether a pointer is host memory (TSLB_HOST, pageable or
- *     pinned) or device memory on the handle's device (TSLB_DEVICE).
+ *     pinned) or device memory on the handle's device (TSLB_DEVICE).  Device
+ *     memory is read and written on the handle's stream only: work of other
+ *     streams that produces an input, or still uses an output buffer, must be
+ *     complete (or ordered before the handle's stream by an event) when the
+ *     call is made.  The Python binding drains PyTorch's current stream
+ *     before passing a CUDA tensor.
  *   - Every call returns TSLB_OK (0) or a negative tslb_status; on error the
  *     handle is unchanged unless stated and tslb_last_error() explains.  No
  *     call aborts the process or traps the device.

@@ -143,6 +143,27 @@ def tslb_create(dims, tau, force=None, bc=(0,) * 6, opt=None, lattice=TSLB_D3Q27
     return h
 
 
+def _device_ptr(t):
+    """Pointer of a CUDA tensor for a call that reads or writes it on the
+    handle's own stream.  Work queued on PyTorch's current stream may still be
+    producing the tensor (or, for freshly allocated memory, still reading what
+    the allocator handed back), so that stream is drained first."""
+    import torch
+    torch.cuda.current_stream(t.device).synchronize()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _out_ptr(a):
+    """Pointer of an output array: numpy, CPU tensor or CUDA tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        return _device_ptr(a)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
 def _ptr(a, dtype):
     """Return (pointer, where, keepalive) for a numpy array or a CUDA torch tensor."""
     if a is None:
@@ -153,7 +174,7 @@ def _ptr(a, dtype):
         t = a.contiguous()
         if t.dtype != want:
             raise TypeError("expected %s tensor" % want)
-        return ctypes.c_void_p(t.data_ptr()), DEVICE, t
+        return _device_ptr(t), DEVICE, t
     if hasattr(a, "numpy"):  # CPU torch tensor (pinned or pageable)
         t = a.contiguous()
         return ctypes.c_void_p(t.data_ptr()), HOST, t
@@ -193,22 +214,12 @@ def tslb_init_moments_f32(h, drho, u, pi=None):
 
 
 def tslb_get_moments_f32(h, drho=None, u=None, pi=None, where=HOST):
-    def p(a):
-        if a is None:
-            return None
-        if hasattr(a, "data_ptr"):
-            return ctypes.c_void_p(a.data_ptr())
-        return ctypes.c_void_p(a.ctypes.data)
+    p = _out_ptr
     _check(load().tslb_get_moments_f32(h, p(drho), p(u), p(pi), int(where)), h)
 
 
 def tslb_get_moments(h, rho=None, u=None, pi=None, where=HOST):
-    def p(a):
-        if a is None:
-            return None
-        if hasattr(a, "data_ptr"):
-            return ctypes.c_void_p(a.data_ptr())
-        return ctypes.c_void_p(a.ctypes.data)
+    p = _out_ptr
     _check(load().tslb_get_moments(h, p(rho), p(u), p(pi), int(where)), h)
 
 
@@ -221,8 +232,7 @@ def tslb_diagnostics(h):
 
 
 def tslb_adjoint_force_gradient(h, nsteps, dJdF, where=HOST):
-    p = ctypes.c_void_p(dJdF.data_ptr() if hasattr(dJdF, "data_ptr") else dJdF.ctypes.data)
-    _check(load().tslb_adjoint_force_gradient(h, int(nsteps), p, int(where)), h)
+    _check(load().tslb_adjoint_force_gradient(h, int(nsteps), _out_ptr(dJdF), int(where)), h)
 
 
 def tslb_diagnostics_noalloc(rho, u, pi, dims, bc, tau, out, stream=None):

@@ -129,6 +129,9 @@ __global__ void __launch_bounds__(NT2) step2d_kernel(const float* __restrict__ s
         }
         commit2();
     };
+    // Launched with programmatic stream serialisation: global memory only
+    // after the preceding step's grid has completed (see the factored kernel).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
     for (int q = 0; q < AHEAD2; ++q) fetch(q);
 
@@ -339,8 +342,16 @@ cudaError_t launch_step2d(const tslb_s* h, const void* src, void* dst, const Phy
     nchunk = (g.ny + ychunk - 1) / ychunk;
     const long long warps = (long long)ntx * nchunk;
     const unsigned blocks = (unsigned)((warps + WARPS2 - 1) / WARPS2);
-    step2d_kernel<<<blocks, NT2, 0, h->stream>>>((const float*)src, (float*)dst, g, p, ychunk, ntx);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(NT2);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step2d_kernel, (const float*)src, (float*)dst, g, p, ychunk, ntx);
 }
 
 cudaError_t launch_encode2d(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst) {

@@ -719,6 +719,13 @@ __global__ void __launch_bounds__(NT, 1)
     c.z1 = min(c.z0 + zchunk, g.nz);
     c.np = c.z1 - c.z0 + 2;
 
+    // Launched with programmatic stream serialisation: the set-up above
+    // touches only shared memory and parameters and may overlap the end of
+    // the preceding step; global memory is read and written only after that
+    // step's grid has completed and its writes are visible.  (No early
+    // trigger: the next grid starts as this one exits.  Triggering at the
+    // start or before the last planes measured slower.)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     K::template prefetch<0>(c, g, p, src, pfb, 0);
     f2 ppA[4], ppB[4], cA[4], cB[4];
 #pragma unroll
@@ -773,9 +780,17 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
     }
     const int zchunk = (g.nz + best_n - 1) / best_n;
     const unsigned bz = (unsigned)((g.nz + zchunk - 1) / zchunk);
-    kern<<<dim3(bx, by, bz), NT, SMEM, h->stream>>>((const typename Codec::T*)src, (typename Codec::T*)dst, g, p,
-                                                   zchunk);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(bx, by, bz);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, (const typename Codec::T*)src, (typename Codec::T*)dst, g, p, zchunk);
 }
 
 template <class Codec>

@@ -49,3 +49,33 @@ def test_context_manager_releases_the_handle(cuda_ok):
         s.init_moments(*W.rest_state((8, 8, 8)))
         s.step(2)
     assert s.handle is None
+
+
+def test_device_inputs_are_ordered_after_the_torch_stream(cuda_ok):
+    """CUDA tensors handed to a solver on its own stream are read only after
+    the work queued on PyTorch's current stream has run: the inputs below are
+    NaN until a fill that waits behind a 25 ms spin on that stream, so an
+    unordered read would find NaNs (and the force field would not be the
+    one filled)."""
+    import torch
+    dims = (64, 32, 16)
+    N = dims[0] * dims[1] * dims[2]
+    st = torch.cuda.Stream()
+    with T.Solver(dims, 0.6, stream=st.cuda_stream) as s:
+        drho = torch.full((N,), float("nan"), dtype=torch.float32, device="cuda")
+        u = torch.full((3, N), float("nan"), dtype=torch.float32, device="cuda")
+        F = torch.full((3 * N,), float("nan"), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        torch.cuda._sleep(50_000_000)  # a bounded spin of 5e7 clock cycles on the current stream
+        drho.fill_(0.0)
+        u.fill_(0.01)
+        F.fill_(0.0)
+        s.init_moments_f32(drho, u)
+        torch.cuda._sleep(50_000_000)
+        F.fill_(1e-6)
+        s.set_force_field(F)
+        s.step(3)
+        d, code = s.diagnostics()
+        assert code == T.TSLB_OK and d["nonfinite"] == 0
+        _, uu, _ = s.get_moments()
+        assert np.allclose(uu[0], 0.01 + 3e-6, rtol=0, atol=1e-8)

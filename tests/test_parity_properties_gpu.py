@@ -3,8 +3,9 @@
 Each example draws a full-lattice box of 3-40 x 4-40 x 3-12 nodes (ragged
 against the factored kernel's 30 x 16 tiles), one of the face sets the library
 supports (jet faces with uniform or Gaussian inflow noise and, with periodic
-sides, a sponge layer), the forcing scheme where it applies, the storage
-type, a relaxation time and a seed; it runs two steps from random moments on
+sides, a sponge layer), the forcing scheme where it applies, a uniform force
+or a per-node force field (outside the jet), the storage type, a relaxation
+time and a seed; it runs two steps from random moments on
 the GPU (either kernel) and on the FP64 oracle and compares every interior
 field.  Bounds: FP32 4e-6 relative per field, twice the one-step bound of
 random moments (FP32 rounding of one step is below 2e-6); BF16 2e-2, about
@@ -50,8 +51,9 @@ def _mask(dims, bc):
        tau=st.floats(0.55, 1.5), seed=st.integers(0, 10 ** 6),
        kernel=st.sampled_from([T.KERNEL_FACTORED, T.KERNEL_DIRECT]),
        F=st.tuples(*[st.floats(-2e-5, 2e-5)] * 3), guo=st.booleans(), bf16=st.booleans(),
-       gauss=st.booleans(), sponge=st.booleans())
-def test_two_steps_match_the_oracle(cuda_ok, nx, ny, nz, faces, tau, seed, kernel, F, guo, bf16, gauss, sponge):
+       gauss=st.booleans(), sponge=st.booleans(), field=st.booleans())
+def test_two_steps_match_the_oracle(cuda_ok, nx, ny, nz, faces, tau, seed, kernel, F, guo, bf16, gauss, sponge,
+                                    field):
     bc = FACES[faces]
     if bc[0] != 0 and nx < 4:
         nx = 4
@@ -59,7 +61,12 @@ def test_two_steps_match_the_oracle(cuda_ok, nx, ny, nz, faces, tau, seed, kerne
     if jet:
         nz = max(nz, 5)
         F = (0.0, 0.0, 0.0)
+        field = False
     dims = (nx, ny, nz)
+    Ff = None
+    if field:  # replaces the uniform force
+        F = (0.0, 0.0, 0.0)
+        Ff = (2e-5 * np.random.default_rng(seed + 1).uniform(-1, 1, (3, nx * ny * nz))).astype(np.float32)
     inflow = dict(center2=(nx // 2, ny // 2), diameter=max(2, min(nx, ny) // 2), u_jet=0.05, noise_amp=0.01,
                   seed=seed % 97, noise="gaussian" if gauss else "uniform") if jet else None
     sp = (2, 50.0) if (jet and bc[0] == 0 and sponge) else None
@@ -67,12 +74,16 @@ def test_two_steps_match_the_oracle(cuda_ok, nx, ny, nz, faces, tau, seed, kerne
     prec = T.BF16 if bf16 else T.FP32
     state = W.random_state(dims, seed=seed, drho=0.002, du=0.01, dpi=1e-4) if jet else W.random_state(dims, seed=seed)
     o = oracle.OracleSim(dims, tau, force=F, bc=bc, inflow=inflow, sponge=sp, forcing=forcing)
+    if Ff is not None:  # before the moments: Guo's initial populations depend on it
+        o.set_force_field(Ff.astype(np.float64))
     o.init_moments(*state)
     o.step(2)
     r0, u0, p0 = o.get_moments()
     s = T.Solver(dims, tau, force=F, bc=bc, kernel=kernel, inflow=inflow, sponge=sp, forcing=forcing,
                  precision=prec, pi_ref=W.pi_reference(state))
     s.init_moments(*state)
+    if Ff is not None:
+        s.set_force_field(Ff)
     s.step(2)
     r1, u1, p1 = s.get_moments()
     s.close()
@@ -81,4 +92,4 @@ def test_two_steps_match_the_oracle(cuda_ok, nx, ny, nz, faces, tau, seed, kerne
     got = np.concatenate([(r1 - 1.0)[None], u1, p1])[:, m]
     for f in range(10):
         e = np.linalg.norm(got[f] - ref[f]) / np.linalg.norm(ref[f])
-        assert e <= (2e-2 if bf16 else 4e-6), (f, e, dims, faces, tau, kernel, forcing, bf16)
+        assert e <= (2e-2 if bf16 else 4e-6), (f, e, dims, faces, tau, kernel, forcing, bf16, field)
