@@ -65,6 +65,9 @@ def test_device_inputs_are_ordered_after_the_torch_stream(cuda_ok):
         drho = torch.full((N,), float("nan"), dtype=torch.float32, device="cuda")
         u = torch.full((3, N), float("nan"), dtype=torch.float32, device="cuda")
         F = torch.full((3 * N,), float("nan"), dtype=torch.float32, device="cuda")
+        # one ordered call first, so the library's first-call set-up cannot
+        # stand in for the wait below
+        s.init_moments_f32(torch.zeros_like(drho), torch.zeros_like(u))
         torch.cuda.synchronize()
         torch.cuda._sleep(50_000_000)  # a bounded spin of 5e7 clock cycles on the current stream
         drho.fill_(0.0)
