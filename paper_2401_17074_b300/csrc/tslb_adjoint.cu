@@ -58,6 +58,23 @@ __device__ __forceinline__ void finish_transpose(const float m[NFIELDS], const f
     for (int c = 0; c < 6; ++c) gb[4 + c] = l[F_PXX + c] * k;
 }
 
+// Gbar layout in its 10 * fs floats: J_a and S_aa are needed together (by
+// exactly the directions with c_a != 0), so they are stored as pairs.
+//   G0 [fs] | (Jx, Sxx) float2 [fs] | (Jy, Syy) | (Jz, Szz) | Sxy [fs] | Sxz [fs] | Syz [fs]
+// gs_off(a): float offset, in units of fs, of scalar array a (G0, Sxy, Sxz,
+// Syz); gp_off(a): that of the pair array of axis a.
+__host__ __device__ constexpr int gs_off(int a) { return a == 0 ? 0 : 6 + a; }
+__host__ __device__ constexpr int gp_off(int a) { return 1 + 2 * a; }
+__device__ __forceinline__ void store_gbar(float* __restrict__ G, long long fs, long long n, const float gb[NFIELDS]) {
+    G[n] = gb[0];
+    reinterpret_cast<float2*>(G + 1 * fs)[n] = make_float2(gb[1], gb[4]);
+    reinterpret_cast<float2*>(G + 3 * fs)[n] = make_float2(gb[2], gb[5]);
+    reinterpret_cast<float2*>(G + 5 * fs)[n] = make_float2(gb[3], gb[6]);
+    G[7 * fs + n] = gb[7];
+    G[8 * fs + n] = gb[8];
+    G[9 * fs + n] = gb[9];
+}
+
 // Final step: lambda = dJ/dm with dJ/d(rho-1) = |u|^2 / 2, dJ/du = rho u,
 // dJ/dPi = 0, and the Gbar of the last forward step from it.
 template <class Codec>
@@ -74,8 +91,7 @@ __global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __r
 #pragma unroll
     for (int k = 0; k < 6; ++k) l[F_PXX + k] = 0.0f;
     finish_transpose(m, l, gb);
-#pragma unroll
-    for (int f = 0; f < NFIELDS; ++f) gbar[f * g.fstride + n] = gb[f];
+    store_gbar(gbar, g.fstride, n, gb);
 }
 
 // Gather blocks: AX x AY x AZ nodes (x fastest), halo tile HX x HY x HZ.
@@ -84,6 +100,10 @@ __global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __r
 constexpr int AX = 32, AY = 4, AZ = 2, AT = AX * AY * AZ;
 constexpr int HX = AX + 2, HY = AY + 2, HZ = AZ + 2;
 constexpr int PX = 40, XOFF = 3, HC = PX * HY * HZ;
+// The tile: the four scalar arrays, float [4][HC], then the three pair arrays,
+// float2 [3][HC], in the order of gs_off and gp_off.
+constexpr int TILE_FLOATS = 4 * HC + 3 * 2 * HC;
+static_assert(TILE_FLOATS == NFIELDS * HC, "ten floats per tile cell");
 // Row copies of the 16-byte tile load: AX / 4 vector pieces and two halo cells.
 constexpr int PIECES = AX / 4 + 2;
 static_assert(HY * HZ * PIECES <= AT, "one row piece per thread");
@@ -108,7 +128,8 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     // fields, staged in shared memory with periodic wrap (cp.async copies, all
     // of a thread's in flight at once, no register round trip); the 27
     // directions then read it at constant offsets from the thread's cell.
-    __shared__ __align__(16) float tile[NFIELDS * HC];
+    __shared__ __align__(16) float tile[TILE_FLOATS];
+    float2* const tileP = reinterpret_cast<float2*>(tile + 4 * HC);
     const int tx = threadIdx.x % AX, ty = (threadIdx.x / AX) % AY, tz = threadIdx.x / (AX * AY);
     const int ox = (int)blockIdx.x * AX, oy = (int)blockIdx.y * AY, oz = (int)blockIdx.z * AZ;  // block origin
     const long long fs = g.fstride;
@@ -123,23 +144,38 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
             gy = gy < 0 ? gy + g.ny : (gy >= g.ny ? gy - g.ny : gy);
             gz = gz < 0 ? gz + g.nz : (gz >= g.nz ? gz - g.nz : gz);
             // halo cells first (s = 0: x = ox - 1, s = 1: x = ox + AX), then
-            // the 16-byte pieces of columns ox + 4 (s - 2) ...
-            int hx = s == 0 ? 0 : (s == 1 ? HX - 1 : 1 + 4 * (s - 2));
+            // the groups of four columns ox + 4 (s - 2) ...
+            const int hx = s == 0 ? 0 : (s == 1 ? HX - 1 : 1 + 4 * (s - 2));
             int gx = ox - 1 + hx;
             gx = gx < 0 ? gx + g.nx : (gx >= g.nx ? gx - g.nx : gx);
             const unsigned gi = (unsigned)gx + (unsigned)g.nx * (unsigned)gy + (unsigned)g.plane * (unsigned)gz;
-            const float* G = gbar + gi;
-            unsigned dst = (unsigned)__cvta_generic_to_shared(&tile[(hz * HY + hy) * PX + XOFF + hx]);
+            const int cell = row * PX + XOFF + hx;
+            const unsigned dS = (unsigned)__cvta_generic_to_shared(&tile[cell]);
+            const unsigned dP = (unsigned)__cvta_generic_to_shared(&tileP[cell]);
             if (s >= 2) {
                 if (TSLB_IN_RANGE(gi + 3, total, p.err)) {
 #pragma unroll
-                    for (int f = 0; f < NFIELDS; ++f, dst += 4 * HC)
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(G + f * fs) : "memory");
+                    for (int a = 0; a < 4; ++a)  // four cells of a scalar array: one 16-byte copy
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dS + 4u * a * HC),
+                                     "l"(gbar + gs_off(a) * fs + gi) : "memory");
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {  // four cells of a pair array: two
+                        const float* src = gbar + gp_off(a) * fs + 2ll * gi;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dP + 8u * a * HC), "l"(src)
+                                     : "memory");
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dP + 8u * a * HC + 16u),
+                                     "l"(src + 4) : "memory");
+                    }
                 }
             } else if (TSLB_IN_RANGE(gi, total, p.err)) {
 #pragma unroll
-                for (int f = 0; f < NFIELDS; ++f, dst += 4 * HC)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(G + f * fs) : "memory");
+                for (int a = 0; a < 4; ++a)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dS + 4u * a * HC),
+                                 "l"(gbar + gs_off(a) * fs + gi) : "memory");
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dP + 8u * a * HC),
+                                 "l"(gbar + gp_off(a) * fs + 2ll * gi) : "memory");
             }
         }
     } else {
@@ -154,17 +190,23 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
             gy = gy < 0 ? gy + g.ny : (gy >= g.ny ? gy - g.ny : gy);
             gz = gz < 0 ? gz + g.nz : (gz >= g.nz ? gz - g.nz : gz);
             const unsigned gi = (unsigned)gx + (unsigned)g.nx * (unsigned)gy + (unsigned)g.plane * (unsigned)gz;
-            const float* G = gbar + gi;
-            const bool ok = TSLB_IN_RANGE(gi, total, p.err);
-            float* T = &tile[(hz * HY + hy) * PX + XOFF + hx];
+            const int cell = (hz * HY + hy) * PX + XOFF + hx;
+            if (TSLB_IN_RANGE(gi, total, p.err)) {
+                const unsigned dS = (unsigned)__cvta_generic_to_shared(&tile[cell]);
+                const unsigned dP = (unsigned)__cvta_generic_to_shared(&tileP[cell]);
 #pragma unroll
-            for (int f = 0; f < NFIELDS; ++f) {
-                if (ok) {
-                    const unsigned dst = (unsigned)__cvta_generic_to_shared(T + f * HC);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(G + f * fs) : "memory");
-                } else {
-                    T[f * HC] = 0.0f;
-                }
+                for (int a = 0; a < 4; ++a)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dS + 4u * a * HC),
+                                 "l"(gbar + gs_off(a) * fs + gi) : "memory");
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dP + 8u * a * HC),
+                                 "l"(gbar + gp_off(a) * fs + 2ll * gi) : "memory");
+            } else {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) tile[a * HC + cell] = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) tileP[a * HC + cell] = make_float2(0.0f, 0.0f);
             }
         }
     }
@@ -185,7 +227,9 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     if (!active) return;
-    const float* Tc = tile + (tz + 1) * (PX * HY) + (ty + 1) * PX + XOFF + (tx + 1);
+    const int cc = (tz + 1) * (PX * HY) + (ty + 1) * PX + XOFF + (tx + 1);  // the thread's tile cell
+    const float* Tc = tile + cc;
+    const float2* Pc = tileP + cc;
     float Ab[NMODES];
     float gbv[3][3][3];  // adjoint populations gb(c), [cz + 1][cy + 1][cx + 1]
 #pragma unroll
@@ -194,18 +238,24 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
         for (int cy = -1; cy <= 1; ++cy)
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
-                const float* G = Tc + cz * (PX * HY) + cy * PX + cx;
-                // adjoint population: psi(c) . Gbar(y + c), nonzero terms only
+                const int o = cz * (PX * HY) + cy * PX + cx;
+                const float* G = Tc + o;
+                const float2* P = Pc + o;
+                // adjoint population: psi(c) . Gbar(y + c), nonzero terms only;
+                // P[a * HC] = (J_a, S_aa)
+                const float2 px = cx != 0 ? P[0 * HC] : make_float2(0.f, 0.f);
+                const float2 py = cy != 0 ? P[1 * HC] : make_float2(0.f, 0.f);
+                const float2 pz = cz != 0 ? P[2 * HC] : make_float2(0.f, 0.f);
                 float gb = G[0];
-                if (cx != 0) gb = fmaf((float)cx, G[1 * HC], gb);
-                if (cy != 0) gb = fmaf((float)cy, G[2 * HC], gb);
-                if (cz != 0) gb = fmaf((float)cz, G[3 * HC], gb);
-                if (cx != 0) gb += G[4 * HC];
-                if (cy != 0) gb += G[5 * HC];
-                if (cz != 0) gb += G[6 * HC];
-                if (cx != 0 && cy != 0) gb = fmaf((float)(cx * cy), G[7 * HC], gb);
-                if (cx != 0 && cz != 0) gb = fmaf((float)(cx * cz), G[8 * HC], gb);
-                if (cy != 0 && cz != 0) gb = fmaf((float)(cy * cz), G[9 * HC], gb);
+                if (cx != 0) gb = fmaf((float)cx, px.x, gb);
+                if (cy != 0) gb = fmaf((float)cy, py.x, gb);
+                if (cz != 0) gb = fmaf((float)cz, pz.x, gb);
+                if (cx != 0) gb += px.y;
+                if (cy != 0) gb += py.y;
+                if (cz != 0) gb += pz.y;
+                if (cx != 0 && cy != 0) gb = fmaf((float)(cx * cy), G[1 * HC], gb);
+                if (cx != 0 && cz != 0) gb = fmaf((float)(cx * cz), G[2 * HC], gb);
+                if (cy != 0 && cz != 0) gb = fmaf((float)(cy * cz), G[3 * HC], gb);
                 gbv[cz + 1][cy + 1][cx + 1] = gb;
             }
     // Modes of the adjoint populations, Ab_k = sum_c w(c) phi_k(c) gb(c), one
@@ -316,8 +366,7 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     l[F_PYZ] = lP[1][2];
     float gb[NFIELDS];
     finish_transpose(m, l, gb);
-#pragma unroll
-    for (int f = 0; f < NFIELDS; ++f) gbar_out[f * fs + n] = gb[f];
+    store_gbar(gbar_out, fs, n, gb);
     fbar[n] = fb_old[0] + fb[0];
     fbar[fs + n] = fb_old[1] + fb[1];
     fbar[2 * fs + n] = fb_old[2] + fb[2];
