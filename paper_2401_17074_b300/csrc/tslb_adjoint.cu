@@ -134,6 +134,9 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     const int ox = (int)blockIdx.x * AX, oy = (int)blockIdx.y * AY, oz = (int)blockIdx.z * AZ;  // block origin
     const long long fs = g.fstride;
     [[maybe_unused]] const unsigned total = (unsigned)(g.plane * g.nz);
+    // launched with programmatic stream serialisation: global memory only
+    // after the preceding kernel (a gather or a forward step) has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (VEC) {
         // thread t copies piece t % PIECES of tile row t / PIECES, all ten fields
         const int t = threadIdx.x;
@@ -382,10 +385,18 @@ cudaError_t adj_launch_all(const tslb_s* h, int which, const void* a, const void
     else {
         const dim3 grid((unsigned)((h->g.nx + AX - 1) / AX), (unsigned)((h->g.ny + AY - 1) / AY),
                         (unsigned)((h->g.nz + AZ - 1) / AZ));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(AT);
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         if (h->g.nx % 4 == 0 && h->g.nx >= AX)
-            adj_gather<Codec, true><<<grid, AT, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
-        else
-            adj_gather<Codec, false><<<grid, AT, 0, h->stream>>>((const float*)b, (const T*)a, c, d, h->g, p);
+            return cudaLaunchKernelEx(&cfg, adj_gather<Codec, true>, (const float*)b, (const T*)a, c, d, h->g, p);
+        return cudaLaunchKernelEx(&cfg, adj_gather<Codec, false>, (const float*)b, (const T*)a, c, d, h->g, p);
     }
     return cudaGetLastError();
 }
