@@ -211,7 +211,11 @@ int tslb_set_force_field(tslb_t* h, const float* F, int where);
 
 /* Advance nsteps TSLB steps (Eq. pushLB with Eq. eqts / Eq. noneqts
  * reconstruction, forcing and faces), asynchronously on the handle's stream.
- * Launch errors are reported immediately; the call does not synchronise. */
+ * Launch errors are reported immediately; the call does not synchronise.
+ * Each step is one kernel launched with programmatic stream serialisation:
+ * its set-up may overlap the end of the kernel before it on the stream, but
+ * it reads and writes global memory only after that kernel has completed, so
+ * stream order holds for any work the caller puts on the same stream. */
 int tslb_step(tslb_t* h, int64_t nsteps);
 
 /* Copy the current moments out as full-lattice FP64 arrays (any pointer may
