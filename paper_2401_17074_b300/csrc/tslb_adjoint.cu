@@ -104,7 +104,8 @@ constexpr int PX = 40, XOFF = 3, HC = PX * HY * HZ;
 // float2 [3][HC], in the order of gs_off and gp_off.
 constexpr int TILE_FLOATS = 4 * HC + 3 * 2 * HC;
 static_assert(TILE_FLOATS == NFIELDS * HC, "ten floats per tile cell");
-// Row copies of the 16-byte tile load: AX / 4 vector pieces and two halo cells.
+// Pieces of a tile row in the 16-byte tile load, one thread each: AX / 4 groups
+// of four columns and the two halo cells.
 constexpr int PIECES = AX / 4 + 2;
 static_assert(HY * HZ * PIECES <= AT, "one row piece per thread");
 static_assert((XOFF + 1) % 4 == 0 && PX % 4 == 0 && XOFF + HX <= PX, "aligned block columns");
@@ -117,8 +118,9 @@ static_assert((XOFF + 1) % 4 == 0 && PX % 4 == 0 && XOFF + HX <= PX, "aligned bl
 // (1, 3, 6 or 10 of them for c with 0, 1, 2 or 3 nonzero components), and
 // adds only to the modes whose weight w(c) phi_k(c) is nonzero (phi_1(0) = 0).
 // VEC: nx is a multiple of 4 and at least AX, so a block's columns, wrapped
-// once, are whole aligned groups of 4 and each tile row is AX / 4 16-byte
-// copies plus its two halo cells.
+// once, are whole aligned groups of 4: a group is one 16-byte copy of each
+// scalar array and two of each pair array; the two halo cells are copied
+// alone.
 template <class Codec, bool VEC>
 __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
                                                  const typename Codec::T* __restrict__ m_cur,
