@@ -178,6 +178,18 @@ def make_state(nx, ny, nz):
     return prm, state
 
 
+def host_cpu():
+    """The host CPU's model name (first processor entry of /proc/cpuinfo), or null."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline(prm, seconds, nz_sample=None):
     """Time the FP64 oracle as it stands on a slab of the channel (periodic z) on all host cores."""
     import oracle
@@ -200,7 +212,7 @@ def cpu_baseline(prm, seconds, nz_sample=None):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": nodes * steps / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": "%dx%dx%d slab of the channel (periodic z), %d steps, FP64 populations, %.1f s"
-                      % (nx, ny, nz_s, steps, el)}
+                      % (nx, ny, nz_s, steps, el), "cpu": host_cpu(), "host_cpus": os.cpu_count()}
 
 
 def cpu_other_configs(seconds):
@@ -285,7 +297,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "turbulent channel %dx%dx%d (bounded sample per step)" % (nx, ny, args.nz),
                        "parallelism": "host cores"},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu": host_cpu(), "host_cpus": os.cpu_count()},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

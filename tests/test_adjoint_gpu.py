@@ -44,6 +44,56 @@ def test_adjoint_matches_complex_step(cuda_ok, n):
         assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (trial, d_adj, d_cs)
 
 
+def _complex_step_entry(dims, tau, state, F0, nsteps, a, i):
+    """dJ/dF_a(node i) of the FP64 oracle by the complex step."""
+    v = np.zeros((3, dims[0] * dims[1] * dims[2]))
+    v[a, i] = 1.0
+    h = 1e-30
+    J = oracle.complex_step_energy(dims, tau, (0,) * 6, state[0], state[1], state[2], F0.astype(np.float64), h * v,
+                                   nsteps)
+    return J.imag / h
+
+
+def test_adjoint_every_entry_small_box(cuda_ok):
+    """Every entry of the 3 x 4^3 gradient against the oracle's complex step
+    (a random force field, 16 steps, checkpoints every 4): entry by entry, so
+    an error confined to a few nodes or one component cannot hide in a
+    random projection."""
+    n, nsteps, tau = 4, 16, 0.55
+    dims, state = W.divfree_random(n=n, u_rms=0.02, kmax=1, tau=tau, seed=5)
+    N = n ** 3
+    F0 = (1e-5 * np.random.default_rng(41).uniform(-1, 1, (3, N))).astype(np.float32)
+    s = T.Solver(dims, tau, checkpoint_every=4)
+    s.set_force_field(F0)
+    s.init_moments(*state)
+    s.step(nsteps)
+    g = s.adjoint_force_gradient(nsteps).astype(np.float64).reshape(3, N)
+    s.close()
+    cs = np.array([[_complex_step_entry(dims, tau, state, F0, nsteps, a, i) for i in range(N)] for a in range(3)])
+    assert np.abs(g - cs).max() <= 1e-4 * np.abs(cs).max(), np.abs(g - cs).max() / np.abs(cs).max()
+    assert np.linalg.norm(g - cs) <= 1e-4 * np.linalg.norm(cs)
+
+
+def test_adjoint_single_entries_16(cuda_ok):
+    """Twelve single entries (random component and node) of the 3 x 16^3
+    gradient of the 64-step workload against the oracle's complex step, each
+    within 1e-4 of its own size (floor: 1 % of the largest entry)."""
+    n, nsteps, tau = 16, 64, 0.52
+    dims, state, s = _setup(n, nsteps=nsteps, tau=tau)
+    N = n ** 3
+    F0 = np.zeros((3, N), dtype=np.float32)
+    s.init_moments(*state)
+    s.set_force_field(F0)
+    s.step(nsteps)
+    g = s.adjoint_force_gradient(nsteps).astype(np.float64).reshape(3, N)
+    s.close()
+    rng = np.random.default_rng(43)
+    gmax = np.abs(g).max()
+    for a, i in zip(rng.integers(0, 3, 12), rng.integers(0, N, 12)):
+        cs = _complex_step_entry(dims, tau, state, F0, nsteps, int(a), int(i))
+        assert abs(g[a, i] - cs) <= 1e-4 * max(abs(cs), 0.01 * gmax), (a, i, g[a, i], cs)
+
+
 def _oracle_energy(dims, tau, state, F, nsteps):
     o = oracle.OracleSim(dims, tau)
     o.init_moments(*state)
