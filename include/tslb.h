@@ -239,7 +239,9 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out);
  * array (boundary entries 0).  Synchronises the stream.  The first call
  * allocates a workspace of checkpoint_every moment states plus 23 FP32 values
  * per node, which the handle keeps for later calls until tslb_destroy.
- * Periodic boxes of fewer than 2^31 nodes, Luo forcing, no sponge layer. */
+ * Boxes of fewer than 2^31 nodes with periodic faces, or periodic x and z
+ * with halfway bounce-back walls on the y faces (the channel); Luo forcing, no
+ * sponge layer; TSLB_ERR_UNSUPPORTED otherwise. */
 int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where);
 
 /* ---- Diagnostics without allocation ------------------------------------

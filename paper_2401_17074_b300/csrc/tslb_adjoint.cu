@@ -14,7 +14,9 @@
 // The objective is J = 1/2 sum rho |u|^2 at the final step; the control is a
 // time-constant per-node acceleration field.  Segments between the forward
 // checkpoints are recomputed with the forward kernel (bitwise identical
-// states) and then swept backwards.  Periodic boxes only.
+// states) and then swept backwards.  Periodic faces, or halfway bounce-back
+// walls on the y faces.
+#include <cstring>
 #include <vector>
 
 #include "tslb_internal.cuh"
@@ -117,11 +119,15 @@ static_assert((XOFF + 1) % 4 == 0 && PX % 4 == 0 && XOFF + HX <= PX, "aligned bl
 // a direction loads only the moment sums whose monomial psi_t(c) is nonzero
 // (1, 3, 6 or 10 of them for c with 0, 1, 2 or 3 nonzero components), and
 // adds only to the modes whose weight w(c) phi_k(c) is nonzero (phi_1(0) = 0).
+// WALLS: halfway bounce-back y faces.  A population that the forward step sends
+// from y into the wall comes back to y reversed, so a direction c whose target
+// y + c lies beyond the wall reads psi(-c) . Gbar(y) instead of
+// psi(c) . Gbar(y + c): the thread's own cell, with the odd (J) terms negated.
 // VEC: nx is a multiple of 4 and at least AX, so a block's columns, wrapped
 // once, are whole aligned groups of 4: a group is one 16-byte copy of each
 // scalar array and two of each pair array; the two halo cells are copied
 // alone.
-template <class Codec, bool VEC>
+template <class Codec, bool VEC, bool WALLS>
 __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
                                                  const typename Codec::T* __restrict__ m_cur,
                                                  float* __restrict__ gbar_out, float* __restrict__ fbar, Geometry g,
@@ -233,6 +239,7 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     __syncthreads();
     if (!active) return;
     const int cc = (tz + 1) * (PX * HY) + (ty + 1) * PX + XOFF + (tx + 1);  // the thread's tile cell
+    const bool wall_lo = WALLS && py == 0, wall_hi = WALLS && py == g.ny - 1;  // warp-uniform
     const float* Tc = tile + cc;
     const float2* Pc = tileP + cc;
     float Ab[NMODES];
@@ -243,21 +250,24 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
         for (int cy = -1; cy <= 1; ++cy)
 #pragma unroll
             for (int cx = -1; cx <= 1; ++cx) {
-                const int o = cz * (PX * HY) + cy * PX + cx;
+                // reflected at a y wall: the own cell, J terms negated
+                const bool flip = WALLS && ((cy < 0 && wall_lo) || (cy > 0 && wall_hi));
+                const int o = flip ? 0 : cz * (PX * HY) + cy * PX + cx;
+                const float sj = flip ? -1.0f : 1.0f;
                 const float* G = Tc + o;
                 const float2* P = Pc + o;
                 // adjoint population: psi(c) . Gbar(y + c), nonzero terms only;
                 // P[a * HC] = (J_a, S_aa)
-                const float2 px = cx != 0 ? P[0 * HC] : make_float2(0.f, 0.f);
-                const float2 py = cy != 0 ? P[1 * HC] : make_float2(0.f, 0.f);
-                const float2 pz = cz != 0 ? P[2 * HC] : make_float2(0.f, 0.f);
+                const float2 qx = cx != 0 ? P[0 * HC] : make_float2(0.f, 0.f);
+                const float2 qy = cy != 0 ? P[1 * HC] : make_float2(0.f, 0.f);
+                const float2 qz = cz != 0 ? P[2 * HC] : make_float2(0.f, 0.f);
                 float gb = G[0];
-                if (cx != 0) gb = fmaf((float)cx, px.x, gb);
-                if (cy != 0) gb = fmaf((float)cy, py.x, gb);
-                if (cz != 0) gb = fmaf((float)cz, pz.x, gb);
-                if (cx != 0) gb += px.y;
-                if (cy != 0) gb += py.y;
-                if (cz != 0) gb += pz.y;
+                if (cx != 0) gb = fmaf(sj * cx, qx.x, gb);
+                if (cy != 0) gb = fmaf(sj * cy, qy.x, gb);
+                if (cz != 0) gb = fmaf(sj * cz, qz.x, gb);
+                if (cx != 0) gb += qx.y;
+                if (cy != 0) gb += qy.y;
+                if (cz != 0) gb += qz.y;
                 if (cx != 0 && cy != 0) gb = fmaf((float)(cx * cy), G[1 * HC], gb);
                 if (cx != 0 && cz != 0) gb = fmaf((float)(cx * cz), G[2 * HC], gb);
                 if (cy != 0 && cz != 0) gb = fmaf((float)(cy * cz), G[3 * HC], gb);
@@ -396,9 +406,10 @@ cudaError_t adj_launch_all(const tslb_s* h, int which, const void* a, const void
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (h->g.nx % 4 == 0 && h->g.nx >= AX)
-            return cudaLaunchKernelEx(&cfg, adj_gather<Codec, true>, (const float*)b, (const T*)a, c, d, h->g, p);
-        return cudaLaunchKernelEx(&cfg, adj_gather<Codec, false>, (const float*)b, (const T*)a, c, d, h->g, p);
+        const bool vec = h->g.nx % 4 == 0 && h->g.nx >= AX, walls = h->bc[2] == TSLB_BC_BOUNCEBACK;
+        auto k = vec ? (walls ? adj_gather<Codec, true, true> : adj_gather<Codec, true, false>)
+                     : (walls ? adj_gather<Codec, false, true> : adj_gather<Codec, false, false>);
+        return cudaLaunchKernelEx(&cfg, k, (const float*)b, (const T*)a, c, d, h->g, p);
     }
     return cudaGetLastError();
 }
@@ -417,9 +428,10 @@ cudaError_t adj_launch(const tslb_s* h, int which, const void* a, const void* b,
 int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, std::string* msg) {
     const Geometry& g = h->g;
     const int k = h->checkpoint_every;
+    const bool ywalls = h->bc[2] == TSLB_BC_BOUNCEBACK && h->bc[3] == TSLB_BC_BOUNCEBACK;
     for (int f = 0; f < 6; ++f)
-        if (h->bc[f] != TSLB_BC_PERIODIC) {
-            *msg = "the adjoint supports periodic boxes only";
+        if (h->bc[f] != TSLB_BC_PERIODIC && !(ywalls && (f == 2 || f == 3))) {
+            *msg = "the adjoint supports periodic faces and bounce-back walls on the y faces";
             return TSLB_ERR_UNSUPPORTED;
         }
     if (k <= 0) {
@@ -491,12 +503,22 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
         nvtxRangePop();
         n_end = n_beg;
     }
-    // scatter the interior gradient into the full-lattice [3][N] output
+    // scatter the interior gradient into the full-lattice [3][N] output; with
+    // y walls its interior rows 1 .. ny - 2 of each z plane, the wall layers 0
     if (e == cudaSuccess) {
         const long long fnx = h->dims[0], fny = h->dims[1], fN = fnx * fny * h->dims[2];
         const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-        for (int a = 0; a < 3 && e == cudaSuccess; ++a)
-            e = cudaMemcpyAsync(dJdF + a * fN, fbar + a * fs, sizeof(float) * (size_t)fN, kind, h->stream);
+        if (!ywalls) {
+            for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+                e = cudaMemcpyAsync(dJdF + a * fN, fbar + a * fs, sizeof(float) * (size_t)fN, kind, h->stream);
+        } else {
+            if (where == TSLB_HOST) std::memset(dJdF, 0, sizeof(float) * 3 * (size_t)fN);
+            else e = cudaMemsetAsync(dJdF, 0, sizeof(float) * 3 * (size_t)fN, h->stream);
+            const size_t row = sizeof(float) * (size_t)g.plane;  // the interior rows of one z plane
+            for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+                e = cudaMemcpy2DAsync(dJdF + a * fN + fnx * g.lo[1], sizeof(float) * (size_t)(fnx * fny),
+                                      fbar + a * fs, row, row, (size_t)g.nz, kind, h->stream);
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cleanup();

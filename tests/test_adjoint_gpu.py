@@ -1,6 +1,7 @@
 """Discrete adjoint of the TSLB step against the oracle's complex-step gradient.
 
-J = 1/2 sum rho |u|^2 after 64 steps on a periodic box from a seeded
+J = 1/2 sum rho |u|^2 after 64 steps on a periodic box (and on small channel
+boxes with bounce-back y walls) from a seeded
 divergence-free random velocity (tau = 0.52); control = per-node body-force
 field F (zero).  Directional derivatives <dJ/dF, v> from the GPU adjoint
 (checkpoint every 16 steps, FP32) must agree with Im J(F + i h v) / h of the
@@ -172,6 +173,71 @@ def test_adjoint_ragged_box_with_force(cuda_ok, dims):
         d_cs = J.imag / h
         d_adj = float(np.sum(g * v))
         assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (trial, d_adj, d_cs)
+
+
+@pytest.mark.parametrize("dims", [(40, 10, 6), (13, 9, 5)], ids=["row-copies", "cell-copies"])
+def test_adjoint_bounce_back_walls(cuda_ok, dims):
+    """The channel's halfway bounce-back y walls (8 and 7 interior rows, so
+    ragged against the 4-row gather blocks), a random force field and
+    checkpoint segments of 4 steps: directional derivatives against the
+    oracle's complex step, and zero gradient on the wall layers."""
+    tau, nsteps, bc = 0.6, 12, (0, 0, 1, 1, 0, 0)
+    N = dims[0] * dims[1] * dims[2]
+    state = W.random_state(dims, seed=44, drho=0.002, du=0.02, dpi=1e-4)
+    F0 = (1e-5 * np.random.default_rng(45).uniform(-1, 1, (3, N))).astype(np.float32)
+    s = T.Solver(dims, tau, bc=bc, checkpoint_every=4)
+    s.set_force_field(F0)
+    s.init_moments(*state)
+    s.step(nsteps)
+    g = s.adjoint_force_gradient(nsteps).astype(np.float64)
+    s.close()
+    walls = g.reshape(3, dims[2], dims[1], dims[0])[:, :, [0, -1], :]
+    assert np.all(walls == 0)
+    rng = np.random.default_rng(46)
+    for trial in range(2):
+        v = rng.standard_normal((3, N))
+        h = 1e-30
+        J = oracle.complex_step_energy(dims, tau, bc, state[0], state[1], state[2], F0.astype(np.float64), h * v,
+                                       nsteps)
+        d_cs = J.imag / h
+        d_adj = float(np.sum(g * v))
+        assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (trial, d_adj, d_cs)
+
+
+def test_adjoint_bounce_back_every_entry(cuda_ok):
+    """Every interior entry of the gradient on a 4 x (4 + 2) x 4 channel box
+    with bounce-back y walls against the oracle's complex step."""
+    dims, tau, nsteps, bc = (4, 6, 4), 0.6, 16, (0, 0, 1, 1, 0, 0)
+    N = dims[0] * dims[1] * dims[2]
+    state = W.random_state(dims, seed=47, drho=0.002, du=0.02, dpi=1e-4)
+    F0 = (1e-5 * np.random.default_rng(48).uniform(-1, 1, (3, N))).astype(np.float32)
+    s = T.Solver(dims, tau, bc=bc, checkpoint_every=4)
+    s.set_force_field(F0)
+    s.init_moments(*state)
+    s.step(nsteps)
+    g = s.adjoint_force_gradient(nsteps).astype(np.float64).reshape(3, N)
+    s.close()
+    y = (np.arange(N) // dims[0]) % dims[1]
+    interior = np.nonzero((y > 0) & (y < dims[1] - 1))[0]
+    cs = np.zeros((3, N))
+    for a in range(3):
+        for i in interior:
+            v = np.zeros((3, N))
+            v[a, i] = 1.0
+            J = oracle.complex_step_energy(dims, tau, bc, state[0], state[1], state[2], F0.astype(np.float64),
+                                           1e-30 * v, nsteps)
+            cs[a, i] = J.imag / 1e-30
+    assert np.abs(g - cs).max() <= 1e-4 * np.abs(cs).max(), np.abs(g - cs).max() / np.abs(cs).max()
+
+
+def test_adjoint_rejects_other_faces(cuda_ok):
+    s = T.Solver((8, 8, 8), 0.6, bc=(2, 2, 0, 0, 0, 0), checkpoint_every=4)  # free-slip x faces
+    s.init_moments(*W.random_state((8, 8, 8), seed=49))
+    s.step(4)
+    with pytest.raises(T.TslbError) as ei:
+        s.adjoint_force_gradient(4)
+    assert ei.value.code == T.TSLB_ERR_UNSUPPORTED
+    s.close()
 
 
 def test_adjoint_partial_window_and_errors(cuda_ok):
