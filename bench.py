@@ -526,6 +526,41 @@ def time_adjoint(T, torch, stream, n=128, nsteps=64, k=16, tau=0.52):
             "note": "wall clock; the adjoint recomputes each checkpoint segment"}
 
 
+def time_adjoint_channel(T, torch, stream, prm, state, nsteps=64, k=16):
+    """Forward (with checkpoints) and discrete adjoint on the full channel: the
+    control is a force field equal to the channel's body force, J = 1/2 sum
+    rho |u|^2 after nsteps; bounce-back y walls."""
+    dims = prm["dims"]
+    N = dims[0] * dims[1] * dims[2]
+    s = T.Solver(dims, prm["tau"], bc=prm["bc"], checkpoint_every=k, stream=stream.cuda_stream)
+    F = torch.zeros((3, N), dtype=torch.float32, device="cuda")
+    F[0] = prm["force"][0]
+    g = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+    s.set_force_field(F)
+    s.init_moments(*state)
+    s.step(nsteps)
+    T.tslb_adjoint_force_gradient(s.handle, nsteps, g, T.DEVICE)  # warm-up: workspace allocation
+    torch.cuda.synchronize()
+    s.init_moments(*state)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    s.step(nsteps)
+    s.synchronize()
+    t2 = time.perf_counter()
+    T.tslb_adjoint_force_gradient(s.handle, nsteps, g, T.DEVICE)
+    t3 = time.perf_counter()
+    finite = bool(torch.isfinite(g).all().item())
+    nodes = s.interior_nodes()
+    s.close()
+    del F, g
+    torch.cuda.empty_cache()
+    return {"workload": "turbulent channel %dx%dx%d, bounce-back walls, %d steps, checkpoint every %d"
+                        % (tuple(dims) + (nsteps, k)),
+            "forward_ms": (t2 - t1) * 1e3, "adjoint_ms": (t3 - t2) * 1e3,
+            "adjoint_mlups": nodes * nsteps / (t3 - t2) / 1e6, "gradient_finite": finite,
+            "note": "wall clock; the adjoint recomputes each checkpoint segment"}
+
+
 def time_e2e(T, torch, prm, state, steps, stream, fp32_io=True):
     """End to end through the C ABI: moments in from pinned host memory, K steps,
     moments back to pinned host memory, wall clock.  fp32_io: the FP32 host
@@ -657,6 +692,8 @@ def main():
                  "jet_paper": time_jet_paper(T, torch, stream),
                  "pressure_driven_300M": time_pressure_driven(T, torch, stream),
                  "d2q9_channel": time_channel2d(T, torch, stream, hbm)}
+        if not args.no_adjoint:
+            extra["adjoint_channel"] = time_adjoint_channel(T, torch, stream, prm, state)
     study = None
     if not args.no_precision_study and not args.no_variants and rank == 0:
         study = precision_study(T, torch, stream, prm, state)
