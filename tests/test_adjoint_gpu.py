@@ -230,6 +230,29 @@ def test_adjoint_bounce_back_every_entry(cuda_ok):
     assert np.abs(g - cs).max() <= 1e-4 * np.abs(cs).max(), np.abs(g - cs).max() / np.abs(cs).max()
 
 
+@pytest.mark.parametrize("prec, ur", [(T.BF16, 2.0 ** -8), (T.FP16, 2.0 ** -11)], ids=["bf16", "fp16"])
+def test_adjoint_16bit_storage(cuda_ok, prec, ur):
+    """With 16-bit moment storage the adjoint differentiates the FP32 step
+    arithmetic along the stored (rounded) trajectory.  Each step rounds every
+    stored value once (unit roundoff ur); the gradient is a smooth function of
+    that trajectory, and its relative L2 difference from the FP32 run's is of
+    the order of one rounding (measured 0.67 ur for BF16 and for FP16 at 16^3,
+    64 steps: the roundings do not accumulate like a random walk).  Bound:
+    4 ur."""
+    n, nsteps, tau = 16, 64, 0.52
+    grads = {}
+    for p in (T.FP32, prec):
+        dims, state = W.divfree_random(n=n, u_rms=0.02, kmax=5, tau=tau, seed=5)
+        s = T.Solver(dims, tau, checkpoint_every=16, precision=p, u_ref=0.05, pi_ref=W.pi_reference(state))
+        s.init_moments(*state)
+        s.set_force_field(np.zeros((3, n ** 3), dtype=np.float32))
+        s.step(nsteps)
+        grads[p] = s.adjoint_force_gradient(nsteps).astype(np.float64)
+        s.close()
+    err = np.linalg.norm(grads[prec] - grads[T.FP32]) / np.linalg.norm(grads[T.FP32])
+    assert err <= 4 * ur, err
+
+
 def test_adjoint_rejects_other_faces(cuda_ok):
     s = T.Solver((8, 8, 8), 0.6, bc=(2, 2, 0, 0, 0, 0), checkpoint_every=4)  # free-slip x faces
     s.init_moments(*W.random_state((8, 8, 8), seed=49))
