@@ -230,9 +230,10 @@ __global__ void __launch_bounds__(AT) adj_gather(const float* __restrict__ gbar,
     load_m<Codec>(m_cur, g.fstride, n, p, m);
     float F[3] = {p.F[0], p.F[1], p.F[2]};
     if (p.force) {
-        F[0] = p.force[n];
-        F[1] = p.force[g.fstride + n];
-        F[2] = p.force[2 * g.fstride + n];
+        const float4 f = reinterpret_cast<const float4*>(p.force)[n];
+        F[0] = f.x;
+        F[1] = f.y;
+        F[2] = f.z;
     }
     const float fb_old[3] = {fbar[n], fbar[fs + n], fbar[2 * fs + n]};
     asm volatile("cp.async.wait_group 0;" ::: "memory");

@@ -477,25 +477,32 @@ int tslb_set_force_field(tslb_t* h, const float* F, int where) {
     const tslb::Geometry& g = h->g;
     cudaError_t e;
     if (!h->force_field) {
-        e = dev_alloc((void**)&h->force_field, sizeof(float) * 3 * g.fstride);
+        e = dev_alloc((void**)&h->force_field, sizeof(float) * 4 * g.fstride);
         if (e != cudaSuccess) {
             h->force_field = nullptr;
             return fail(h, TSLB_ERR_ALLOC, "force field allocation failed");
         }
     }
-    // Gather the interior of the full-lattice [3][N] array row by row.
+    // Gather the interior of the full-lattice [3][N] array row by row into a
+    // planar staging array, then interleave it into one float4 per node.
+    float* planar = nullptr;
+    e = dev_alloc_async((void**)&planar, sizeof(float) * 3 * g.fstride, h->stream);
+    if (e != cudaSuccess) return fail(h, TSLB_ERR_ALLOC, "force field staging allocation failed");
     const long long fnx = h->dims[0], fny = h->dims[1], fN = fnx * fny * h->dims[2];
     const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         const float* srcA = F + a * fN;
-        float* dstA = h->force_field + a * g.fstride;
+        float* dstA = planar + a * g.fstride;
         for (int z = 0; z < g.nz; ++z) {
             const float* s = srcA + g.lo[0] + fnx * (g.lo[1] + fny * (long long)(z + g.lo[2]));
             e = cudaMemcpy2DAsync(dstA + g.plane * z, sizeof(float) * g.nx, s, sizeof(float) * fnx,
                                   sizeof(float) * g.nx, g.ny, kind, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "force field copy");
+            if (e != cudaSuccess) break;
         }
     }
+    if (e == cudaSuccess) e = tslb::launch_pack_force(h, planar, h->force_field);
+    cudaFreeAsync(planar, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "force field copy");
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "force field synchronize");
     return TSLB_OK;

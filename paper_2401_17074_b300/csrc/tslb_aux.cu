@@ -224,4 +224,20 @@ cudaError_t launch_diag(const tslb_s* h, const void* src, const Physics& p, doub
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void pack_force_kernel(const float* __restrict__ planar, float4* __restrict__ packed, long long fs,
+                                  long long total) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= total) return;
+    packed[n] = make_float4(planar[n], planar[fs + n], planar[2 * fs + n], 0.0f);
+}
+}  // namespace
+
+cudaError_t launch_pack_force(const tslb_s* h, const float* planar, float* packed) {
+    const long long total = h->g.plane * h->g.nz;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    pack_force_kernel<<<blocks, 256, 0, h->stream>>>(planar, reinterpret_cast<float4*>(packed), h->g.fstride, total);
+    return cudaGetLastError();
+}
+
 }  // namespace tslb

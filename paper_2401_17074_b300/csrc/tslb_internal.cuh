@@ -59,7 +59,7 @@ struct Geometry {
 struct Physics {
     float omega1;          // 1 - omega
     float F[3];            // constant acceleration
-    const float* force;    // per-node acceleration [3][fstride] or nullptr
+    const float* force;    // per-node acceleration, one float4 (F_x, F_y, F_z, 0) per stored node, or nullptr
     // inflow (z- face)
     long long in_c2[2];
     long long in_d;
@@ -573,6 +573,8 @@ bool factored_supports(const tslb_s* h);
 cudaError_t launch_encode(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst,
                           const Physics& p);
 cudaError_t launch_decode(const tslb_s* h, const void* src, double* rho, double* u, double* pi, const Physics& p);
+// Interleave a planar [3][fstride] force field into one float4 per stored node.
+cudaError_t launch_pack_force(const tslb_s* h, const float* planar, float* packed);
 cudaError_t launch_diag(const tslb_s* h, const void* src, const Physics& p, double* out_dev);
 
 Physics make_physics(const tslb_s* h);

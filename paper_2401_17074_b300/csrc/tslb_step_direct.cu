@@ -32,9 +32,10 @@ __device__ __forceinline__ void node_modes(const typename Codec::T* __restrict__
     load_node<Codec>(src, g, p, idx, m);
     float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
     if (p.force) {
-        F0 = p.force[idx];
-        F1 = p.force[g.fstride + idx];
-        F2 = p.force[2 * g.fstride + idx];
+        const float4 f = reinterpret_cast<const float4*>(p.force)[idx];
+        F0 = f.x;
+        F1 = f.y;
+        F2 = f.z;
     }
     post_modes(m[F_DRHO], m[F_UX], m[F_UY], m[F_UZ], m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], F0, F1, F2,
                omega1_at(p, zfull), A, p.guo != 0);
@@ -129,9 +130,10 @@ __global__ void __launch_bounds__(256) step_direct_kernel(const typename Codec::
     if (p.guo) {
         float F0 = p.F[0], F1 = p.F[1], F2 = p.F[2];
         if (p.force) {
-            F0 = p.force[n];
-            F1 = p.force[g.fstride + n];
-            F2 = p.force[2 * g.fstride + n];
+            const float4 f = reinterpret_cast<const float4*>(p.force)[n];
+            F0 = f.x;
+            F1 = f.y;
+            F2 = f.z;
         }
         guo_finish(out, F0, F1, F2, 1.0f);
     }

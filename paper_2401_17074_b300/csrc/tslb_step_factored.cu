@@ -78,8 +78,8 @@ constexpr int NCORR = 8;
 constexpr size_t CORRBUF = sizeof(float) * 2 * 2 * NCORR * 32;
 // Exchange mbarriers: [WROWS rows][2 buffers].
 constexpr size_t BARBUF = sizeof(uint64_t) * WROWS * 2;
-// With a force field: [2 buffers][NT threads] slots of the node's three force
-// components (16 bytes each), prefetched with the moments.
+// With a force field: [2 buffers][NT threads] slots of the node's force
+// (the stored float4, 16 bytes each), prefetched with the moments.
 constexpr size_t FSLOT = 16;
 constexpr size_t FBUF = FSLOT * NT;
 template <int E, bool FORCE>
@@ -313,9 +313,10 @@ __device__ __forceinline__ void load_force(const Physics& p, const Geometry& g, 
     F1 = p.F[1];
     F2 = p.F[2];
     if (p.force && TSLB_IN_RANGE(idx, g.plane * g.nz, p.err)) {
-        F0 = __ldg(p.force + idx);
-        F1 = __ldg(p.force + g.fstride + idx);
-        F2 = __ldg(p.force + 2 * g.fstride + idx);
+        const float4 f = __ldg(reinterpret_cast<const float4*>(p.force) + idx);
+        F0 = f.x;
+        F1 = f.y;
+        F2 = f.z;
     }
 }
 
@@ -369,12 +370,9 @@ struct Kernel {
             cp_async<PF::B01>(smem_u32(b + c.tid * PF::B01), src + (size_t)n * 4);
             cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * g.fstride + (size_t)n * 4);
             cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * g.fstride + (size_t)n * 2);
-            if (FORCE) {
-                const uint32_t f = smem_u32(pfb + FOFF + PAR * FBUF + c.tid * FSLOT);
-                cp_async<4>(f, p.force + n);
-                cp_async<4>(f + 4, p.force + g.fstride + n);
-                cp_async<4>(f + 8, p.force + 2 * g.fstride + n);
-            }
+            if (FORCE)
+                cp_async<16>(smem_u32(pfb + FOFF + PAR * FBUF + c.tid * FSLOT),
+                             reinterpret_cast<const float4*>(p.force) + n);
         }
         cp_async_commit();
     }
