@@ -209,7 +209,9 @@ def cpu_baseline(prm, seconds, nz_sample=None):
         el = time.perf_counter() - t0
         if el >= seconds or steps >= 1000:
             break
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # the oracle's step runs its (z, y) rows in parallel: every thread of the
+    # team has work when there are at least as many rows as threads
+    cores = min(oracle.threads(), nz_s * (ny - 2))
     return {"value": nodes * steps / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": "%dx%dx%d slab of the channel (periodic z), %d steps, FP64 populations, %.1f s"
                       % (nx, ny, nz_s, steps, el), "cpu": host_cpu(), "host_cpus": os.cpu_count()}
@@ -290,7 +292,7 @@ def run_reference(args):
     el = time.perf_counter() - t0
     nodes = sx * (ny - 2) * nzs
     v = nodes * args.steps / el / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = min(oracle.threads(), nzs * (ny - 2))
     sample = "%dx%dx%d sub-box of the channel (periodic x, z), FP64 populations, %d steps" % (sx, ny, nzs, args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,

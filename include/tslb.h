@@ -244,13 +244,33 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out);
  * sponge layer; TSLB_ERR_UNSUPPORTED otherwise. */
 int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where);
 
+/* Gradient dJ/dF of any objective J of the final moments with respect to the
+ * time-constant per-node body-force field (Luo term of Sec. 3.1), through the
+ * last `nsteps` steps -- the discrete adjoint of the step of Sec. 2.1-2.2
+ * (Eq. eqts, Eq. noneqts, Eq. pushLB), run backwards from the caller's seed.
+ * lambda_T is the cotangent dJ/dm of the current (final) moments as a
+ * full-lattice FP64 [10][N] array: rows rho (equally rho - 1), u_x, u_y, u_z,
+ * Pi_xx, Pi_yy, Pi_zz, Pi_xy, Pi_xz, Pi_yz, each the derivative with respect
+ * to the stored component (Pi_xy counted once); boundary-layer entries are
+ * ignored.  The caller keeps ownership; it is read before the call returns.
+ * ckpt_every is 0 or the checkpoint_every the handle was created with
+ * (TSLB_ERR_INVALID otherwise).  dJdF is a full-lattice FP32 [3][N] array
+ * (boundary entries 0).  `where` applies to lambda_T and dJdF.  A host
+ * lambda_T is staged through 80 bytes per lattice node of device memory that
+ * the handle allocates on first use and keeps until tslb_destroy.  Otherwise
+ * as tslb_adjoint_force_gradient, which is the special case
+ * lambda = (|u|^2/2, rho u, 0) of J = 1/2 sum rho |u|^2.  Synchronises the
+ * stream. */
+int tslb_adjoint(tslb_t* h, const double* lambda_T, int64_t nsteps, int ckpt_every, float* dJdF, int where);
+
 /* ---- Diagnostics without allocation ------------------------------------
- * The paper has no counterpart of this call.  It serves callers that must not
- * allocate device memory at the point where they want the numbers: code that
- * runs while its stream is being captured into a CUDA graph (allocation calls
- * are not allowed inside a capture), real-time loops that forbid allocator
- * calls, or programs whose framework allocator has already reserved the
- * device memory.
+ * The paper has no counterpart of this call.  It serves callers that cannot
+ * allocate device memory at the point where they want the numbers: programs
+ * run under a fixed device-memory budget that is already spent, programs whose
+ * framework allocator has reserved all of the device's memory up front (a
+ * plain cudaMalloc then fails although the framework holds free blocks), and
+ * latency-bound loops between solver steps, where cudaMalloc / cudaFree, which
+ * may synchronise the whole device, are not acceptable.
  *
  * tslb_diagnostics_noalloc computes the same FP64 sums as tslb_diagnostics
  * over moment arrays the caller owns: rho[N], u[3][N] and pi[6][N] (pi may be
@@ -266,9 +286,14 @@ int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int wher
  * partial sums live in a fixed 256 KB __device__ array that every device
  * loading this library holds until the process exits.  Consequences:
  *   - at most TSLB_NOALLOC_MAX_NODES interior nodes; more return TSLB_ERR_INVALID;
- *   - the first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress, with that device current; make that first call
- *     before any stream capture;
+ *   - the first call on a device does the set-up: it looks up the array's
+ *     device address with cudaGetSymbolAddress, with that device current, and
+ *     keeps it for the life of the process; make that first call before any
+ *     stream capture.  The address belongs to the device's primary context:
+ *     after cudaDeviceReset of that device, do not call this entry point again
+ *     in the same process;
+ *   - a node counts as non-finite when any of its moments (rho, u and, when
+ *     pi is given, the six Pi components) is NaN or Inf;
  *   - every call shares the array: calls that overlap on the GPU (other
  *     streams, other host threads) race and give wrong sums.  Each call
  *     rewrites every partial it reads, so nothing carries over between calls.

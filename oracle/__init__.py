@@ -82,6 +82,10 @@ def lib():
         L.orc2_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         L.orc2_get_moments.argtypes = [ctypes.c_void_p, dp, dp, dp]
         L.orc_complex_run.argtypes = [i64p, ctypes.c_double, ip, dp, dp, dp, dp, dp, ctypes.c_int64, dp, dp]
+        L.orc_complex_run_moments.argtypes = [i64p, ctypes.c_double, ip, dp, dp, dp, dp, dp, ctypes.c_int64, dp,
+                                              dp]
+        L.orc_threads.argtypes = []
+        L.orc_threads.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -256,6 +260,35 @@ def complex_step_energy(dims, tau, bc, rho, u, pi, F_re, F_im, nsteps):
     if st != 0:
         raise ValueError("oracle rejected the configuration (status %d)" % st)
     return complex(jr.value, ji.value)
+
+
+def complex_step_moments(dims, tau, bc, rho, u, pi, F_re, F_im, nsteps):
+    """Complex final moments after nsteps with the force field F_re + i F_im.
+
+    Returns (rho [N], u [3, N], pi [6, N]) as complex arrays (full lattice,
+    boundary layers at the rest state).  For F_im = h v, Im J(m)/h of any
+    holomorphic objective J is its directional derivative along v.
+    """
+    d = np.array(dims, dtype=np.int64)
+    b = np.array(bc, dtype=np.int32)
+    rho, u = _f64(rho).reshape(-1), _f64(u).reshape(-1)
+    N = rho.size
+    pi = _f64(pi).reshape(-1) if pi is not None else np.zeros(6 * N)
+    F_re, F_im = _f64(F_re).reshape(-1), _f64(F_im).reshape(-1)
+    m_re = np.zeros(10 * N)
+    m_im = np.zeros(10 * N)
+    st = lib().orc_complex_run_moments(d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), float(tau),
+                                       b.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(rho), _d(u), _d(pi),
+                                       _d(F_re), _d(F_im), int(nsteps), _d(m_re), _d(m_im))
+    if st != 0:
+        raise ValueError("oracle rejected the configuration (status %d)" % st)
+    m = m_re + 1j * m_im
+    return m[:N], m[N:4 * N].reshape(3, N), m[4 * N:].reshape(6, N)
+
+
+def threads():
+    """OpenMP threads of the oracle's parallel loops in this process."""
+    return int(lib().orc_threads())
 
 
 # ---- D2Q9 ------------------------------------------------------------------------

@@ -75,6 +75,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <limits>
+#include <omp.h>
 
 namespace {
 
@@ -373,10 +374,12 @@ void step_once(Sim<T>& s) {
     const int64_t zhi = (s.bc[5] == BC_OUTFLOW) ? nz - 1 : s.hi(2);
     const int64_t ylo = (s.bc[2] == BC_NEE_WALL) ? 0 : s.lo(1);
     const int64_t yhi = (s.bc[3] == BC_NEE_WALL) ? s.n[1] - 1 : s.hi(1);
-#pragma omp parallel for schedule(static)
+    // Sources are independent in push form: each (destination, direction)
+    // slot has exactly one source, so (z, y) rows run in parallel.
+#pragma omp parallel for collapse(2) schedule(static)
     for (int64_t z = zlo; z <= zhi; ++z) {
-        T post[27];
-        for (int64_t y = ylo; y <= yhi; ++y)
+        for (int64_t y = ylo; y <= yhi; ++y) {
+            T post[27];
             for (int64_t x = s.lo(0); x <= s.hi(0); ++x) {
                 source_post(s, x, y, z, post);
                 const bool ghost = !s.interior(x, y, z);
@@ -412,19 +415,24 @@ void step_once(Sim<T>& s) {
                     s.fnew[s.idx(d[0], d[1], d[2]) * 27 + Lattice::index(c2[0], c2[1], c2[2])] = post[i];
                 }
             }
+        }
     }
     std::swap(s.f, s.fnew);
     s.t += 1;
 }
 
+// Every interior population must have been written by the step (the buffer
+// is NaN-filled first), so a gap in the streaming rules shows up as NaN.
 template <class T>
 int check_filled(const Sim<T>& s) {
+    int64_t bad = 0;
+#pragma omp parallel for collapse(2) schedule(static) reduction(+ : bad)
     for (int64_t z = s.lo(2); z <= s.hi(2); ++z)
         for (int64_t y = s.lo(1); y <= s.hi(1); ++y)
             for (int64_t x = s.lo(0); x <= s.hi(0); ++x)
                 for (int i = 0; i < 27; ++i)
-                    if (std::isnan(std::real(s.f[s.idx(x, y, z) * 27 + i]))) return -1;
-    return 0;
+                    if (std::isnan(std::real(s.f[s.idx(x, y, z) * 27 + i]))) ++bad;
+    return bad ? -1 : 0;
 }
 
 template <class T>
@@ -612,16 +620,29 @@ int orc_get_populations(void* h, double* f) {
     return 0;
 }
 int64_t orc_time(void* h) { return static_cast<Sim<double>*>(h)->t; }
+// OpenMP threads a parallel step uses (the team size of a parallel region).
+int orc_threads() {
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        n = omp_get_num_threads();
+    }
+    return n;
+}
 
 // ---- complex-step simulation (for derivative checks) ---------------------
 // Runs nsteps from real initial moments with a complex per-node force field
 // (Fre + i Fim, [3][N]) and returns the complex kinetic energy
 // J = 1/2 sum_interior rho |u|^2 written with u.u (no conjugate) so that it
 // stays holomorphic; Im J(F + i h v)/h is the directional derivative dJ/dF.v.
-int orc_complex_run(const int64_t* dims, double tau, const int* bc, const double* rho, const double* u,
-                    const double* pi, const double* Fre, const double* Fim, int64_t nsteps, double* J_re,
-                    double* J_im) {
-    Sim<cplx> s;
+}  // extern "C"
+
+namespace {
+// nsteps of the complex simulation from real initial moments under the
+// complex force field Fre + i Fim; returns a validate_and_init status.
+int complex_sim_run(Sim<cplx>& s, const int64_t* dims, double tau, const int* bc, const double* rho,
+                    const double* u, const double* pi, const double* Fre, const double* Fim, int64_t nsteps) {
     const double F0[3] = {0.0, 0.0, 0.0};
     int st = validate_and_init(&s, dims, tau, F0, bc, nullptr);
     if (st != 0) return st;
@@ -635,6 +656,18 @@ int orc_complex_run(const int64_t* dims, double tau, const int* bc, const double
     for (int64_t k = 0; k < 3 * N; ++k) s.field[k] = cplx(Fre ? Fre[k] : 0.0, Fim ? Fim[k] : 0.0);
     s.has_field = true;
     for (int64_t k = 0; k < nsteps; ++k) step_once(s);
+    return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int orc_complex_run(const int64_t* dims, double tau, const int* bc, const double* rho, const double* u,
+                    const double* pi, const double* Fre, const double* Fim, int64_t nsteps, double* J_re,
+                    double* J_im) {
+    Sim<cplx> s;
+    int st = complex_sim_run(s, dims, tau, bc, rho, u, pi, Fre, Fim, nsteps);
+    if (st != 0) return st;
     cplx J = 0.0;
     for (int64_t z = s.lo(2); z <= s.hi(2); ++z)
         for (int64_t y = s.lo(1); y <= s.hi(1); ++y)
@@ -645,6 +678,25 @@ int orc_complex_run(const int64_t* dims, double tau, const int* bc, const double
             }
     *J_re = J.real();
     *J_im = J.imag();
+    return 0;
+}
+
+// The same run, returning the complex final moments (full lattice, the
+// layout of orc_get_moments: rho [N], u [3][N], pi [6][N], real and imaginary
+// parts in separate [10][N] arrays) so that any holomorphic objective of them
+// can be differentiated by the complex step.
+int orc_complex_run_moments(const int64_t* dims, double tau, const int* bc, const double* rho, const double* u,
+                            const double* pi, const double* Fre, const double* Fim, int64_t nsteps, double* m_re,
+                            double* m_im) {
+    Sim<cplx> s;
+    int st = complex_sim_run(s, dims, tau, bc, rho, u, pi, Fre, Fim, nsteps);
+    if (st != 0) return st;
+    const int64_t N = s.N();
+    std::vector<cplx> r(N), uu(3 * N), p(6 * N);
+    get_moments(&s, r.data(), uu.data(), p.data());
+    for (int64_t k = 0; k < N; ++k) { m_re[k] = r[k].real(); m_im[k] = r[k].imag(); }
+    for (int64_t k = 0; k < 3 * N; ++k) { m_re[N + k] = uu[k].real(); m_im[N + k] = uu[k].imag(); }
+    for (int64_t k = 0; k < 6 * N; ++k) { m_re[4 * N + k] = p[k].real(); m_im[4 * N + k] = p[k].imag(); }
     return 0;
 }
 

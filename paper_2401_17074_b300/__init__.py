@@ -32,9 +32,10 @@ TSLB_FORCING_LUO, TSLB_FORCING_GUO = 0, 1
 TSLB_ROUND_NEAREST, TSLB_ROUND_STOCHASTIC = 0, 1
 
 EXPORTED = [
-    "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_set_force_field", "tslb_step",
-    "tslb_get_moments", "tslb_diagnostics", "tslb_adjoint_force_gradient", "tslb_interior_nodes",
-    "tslb_synchronize", "tslb_destroy", "tslb_last_error", "tslb_diagnostics_noalloc",
+    "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_init_moments_f32", "tslb_set_force_field",
+    "tslb_step", "tslb_get_moments", "tslb_get_moments_f32", "tslb_diagnostics", "tslb_adjoint_force_gradient",
+    "tslb_adjoint", "tslb_interior_nodes", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
+    "tslb_diagnostics_noalloc",
 ]
 NOALLOC_MAX_NODES = 1 << 26
 
@@ -97,6 +98,7 @@ def load(build_if_missing=True):
     L.tslb_get_moments_f32.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     L.tslb_diagnostics.argtypes = [vp, ctypes.POINTER(tslb_diag)]
     L.tslb_adjoint_force_gradient.argtypes = [vp, i64, fp, ctypes.c_int]
+    L.tslb_adjoint.argtypes = [vp, vp, i64, ctypes.c_int, fp, ctypes.c_int]
     L.tslb_interior_nodes.argtypes = [vp]
     L.tslb_interior_nodes.restype = i64
     L.tslb_synchronize.argtypes = [vp]
@@ -235,6 +237,21 @@ def tslb_adjoint_force_gradient(h, nsteps, dJdF, where=HOST):
     _check(load().tslb_adjoint_force_gradient(h, int(nsteps), _out_ptr(dJdF), int(where)), h)
 
 
+def tslb_adjoint(h, lambda_T, nsteps, ckpt_every, dJdF, where=HOST):
+    """dJ/dF for the cotangent lambda_T ([10][N] FP64: rho, u, Pi rows, full lattice).
+
+    lambda_T and dJdF are both host arrays (where=HOST: numpy or CPU tensors) or
+    both CUDA tensors (where=DEVICE)."""
+    if where == DEVICE:
+        lp, lw, keep = _ptr(lambda_T, np.float64)
+        if lw != DEVICE:
+            raise TypeError("lambda_T must be a CUDA float64 tensor with where=DEVICE")
+    else:
+        keep = np.ascontiguousarray(lambda_T, dtype=np.float64)
+        lp = ctypes.c_void_p(keep.ctypes.data)
+    _check(load().tslb_adjoint(h, lp, int(nsteps), int(ckpt_every), _out_ptr(dJdF), int(where)), h)
+
+
 def tslb_diagnostics_noalloc(rho, u, pi, dims, bc, tau, out, stream=None):
     """FP64 diagnostics of caller-owned device moment arrays without any allocation.
 
@@ -242,9 +259,32 @@ def tslb_diagnostics_noalloc(rho, u, pi, dims, bc, tau, out, stream=None):
     tslb_get_moments; out: CUDA float64 tensor of 8 entries.  Asynchronous on
     `stream` (a raw cudaStream_t value, None = default stream).
     """
+    import torch
+    dims = [int(v) for v in dims]
+    if len(dims) != 3 or min(dims) < 1:
+        raise ValueError("dims must be three positive extents")
+    N = dims[0] * dims[1] * dims[2]
+    # every array is checked before the launch: the kernels read N, 3N and 6N
+    # doubles and write 8, with no bounds of their own
+    arrays = (("rho", rho, N), ("u", u, 3 * N), ("pi", pi, 6 * N), ("out", out, 8))
+    for name, a, need in arrays:
+        if a is None and name != "pi":
+            raise ValueError("%s must be given" % name)
+    for name, a, need in arrays:
+        if a is None:
+            continue
+        if not (hasattr(a, "is_cuda") and a.is_cuda):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if a.dtype != torch.float64:
+            raise ValueError("%s must be float64" % name)
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+        if a.numel() < need:
+            raise ValueError("%s holds %d values, %d needed" % (name, a.numel(), need))
+
     def p(a):
         return None if a is None else ctypes.c_void_p(a.data_ptr())
-    d = (ctypes.c_int64 * 3)(*[int(v) for v in dims])
+    d = (ctypes.c_int64 * 3)(*dims)
     b = (ctypes.c_int * 6)(*[int(v) for v in bc])
     s = ctypes.c_void_p(int(stream)) if stream else None
     _check(load().tslb_diagnostics_noalloc(p(rho), p(u), p(pi), d, b, float(tau), s, p(out)), None)
@@ -368,4 +408,16 @@ class Solver:
     def adjoint_force_gradient(self, nsteps):
         g = np.zeros(3 * self.N, dtype=np.float32)
         tslb_adjoint_force_gradient(self._h, nsteps, g, HOST)
+        return g.reshape(3, self.N)
+
+    def adjoint(self, lam, nsteps):
+        """dJ/dF ([3, N] FP32) for the cotangent lam = dJ/dm of the current moments,
+        given as (lam_rho [N], lam_u [3, N], lam_pi [6, N]) or one [10, N] array."""
+        if isinstance(lam, (tuple, list)):
+            lam = np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1) for a in lam])
+        lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
+        if lam.size != 10 * self.N:
+            raise ValueError("the cotangent needs 10 N values")
+        g = np.zeros(3 * self.N, dtype=np.float32)
+        tslb_adjoint(self._h, lam, nsteps, 0, g, HOST)
         return g.reshape(3, self.N)

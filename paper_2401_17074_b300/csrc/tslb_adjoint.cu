@@ -11,8 +11,10 @@
 // lambda(y) and the state m(y) it pairs with are all the next (earlier) step's
 // first map needs, so kernel adj_gather ends with that step's Gbar(y) and the
 // lambda array is never stored; adj_seed does the same for the final step.
-// The objective is J = 1/2 sum rho |u|^2 at the final step; the control is a
-// time-constant per-node acceleration field.  Segments between the forward
+// The objective is any function J of the final moments, entered through its
+// cotangent lambda = dJ/dm (adj_seed_lambda), or J = 1/2 sum rho |u|^2 at the
+// final step (adj_seed); the control is a time-constant per-node acceleration
+// field.  Segments between the forward
 // checkpoints are recomputed with the forward kernel (bitwise identical
 // states) and then swept backwards.  Periodic faces, or halfway bounce-back
 // walls on the y faces.
@@ -92,6 +94,26 @@ __global__ void adj_seed(const typename Codec::T* __restrict__ m_end, float* __r
     l[F_UZ] = rho * m[F_UZ];
 #pragma unroll
     for (int k = 0; k < 6; ++k) l[F_PXX + k] = 0.0f;
+    finish_transpose(m, l, gb);
+    store_gbar(gbar, g.fstride, n, gb);
+}
+
+// Final step with a caller cotangent: lambda = dJ/dm of any objective J of
+// the final moments, given as a full-lattice FP64 [10][N] array (rho, u_x,
+// u_y, u_z, Pi_xx, Pi_yy, Pi_zz, Pi_xy, Pi_xz, Pi_yz; the rho row is also the
+// cotangent of rho - 1), and the Gbar of the last forward step from it.
+template <class Codec>
+__global__ void adj_seed_lambda(const typename Codec::T* __restrict__ m_end, const double* __restrict__ lam,
+                                float* __restrict__ gbar, Geometry g, Physics p, long long fnx, long long fny,
+                                long long fN) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= g.plane * g.nz) return;
+    const long long xi = n % g.nx, yi = (n / g.nx) % g.ny, zi = n / g.plane;
+    const long long node = (xi + g.lo[0]) + fnx * ((yi + g.lo[1]) + fny * (zi + g.lo[2]));
+    float m[NFIELDS], l[NFIELDS], gb[NFIELDS];
+    load_m<Codec>(m_end, g.fstride, n, p, m);
+#pragma unroll
+    for (int f = 0; f < NFIELDS; ++f) l[f] = (float)lam[f * fN + node];
     finish_transpose(m, l, gb);
     store_gbar(gbar, g.fstride, n, gb);
 }
@@ -394,8 +416,15 @@ cudaError_t adj_launch_all(const tslb_s* h, int which, const void* a, const void
     const long long total = h->g.plane * h->g.nz;
     const unsigned blocks = (unsigned)((total + 255) / 256);
     typedef typename Codec::T T;
-    if (which == 0) adj_seed<Codec><<<blocks, 256, 0, h->stream>>>((const T*)a, c, h->g, p);
-    else {
+    if (which == 0) {
+        if (b) {  // caller cotangent (device FP64 [10][N])
+            const long long fnx = h->dims[0], fny = h->dims[1], fN = fnx * fny * h->dims[2];
+            adj_seed_lambda<Codec><<<blocks, 256, 0, h->stream>>>((const T*)a, (const double*)b, c, h->g, p, fnx,
+                                                                  fny, fN);
+        } else {
+            adj_seed<Codec><<<blocks, 256, 0, h->stream>>>((const T*)a, c, h->g, p);
+        }
+    } else {
         const dim3 grid((unsigned)((h->g.nx + AX - 1) / AX), (unsigned)((h->g.ny + AY - 1) / AY),
                         (unsigned)((h->g.nz + AZ - 1) / AZ));
         cudaLaunchConfig_t cfg = {};
@@ -426,7 +455,9 @@ cudaError_t adj_launch(const tslb_s* h, int which, const void* a, const void* b,
 }  // namespace
 
 // Host driver of the adjoint; error text goes to *msg.  Returns a tslb_status.
-int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, std::string* msg) {
+// lambda: the caller's cotangent of the final moments (full-lattice FP64
+// [10][N], host or device per `where`), or null for J = 1/2 sum rho |u|^2.
+int adjoint_run(tslb_s* h, const double* lambda, int64_t nsteps, float* dJdF, int where, std::string* msg) {
     const Geometry& g = h->g;
     const int k = h->checkpoint_every;
     const bool ywalls = h->bc[2] == TSLB_BC_BOUNCEBACK && h->bc[3] == TSLB_BC_BOUNCEBACK;
@@ -458,6 +489,21 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
     // part a multiple of 512 bytes: fs is padded to 128 nodes)
     const size_t gbar_bytes = sizeof(float) * NFIELDS * fs, fbar_bytes = sizeof(float) * 3 * fs;
     const size_t need = 2 * gbar_bytes + fbar_bytes + state_bytes * (size_t)k;
+    // a host cotangent is staged through device memory kept in the handle
+    const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
+    const size_t lam_bytes = sizeof(double) * NFIELDS * (size_t)fN;
+    if (lambda && where == TSLB_HOST && h->adj_lam_bytes < lam_bytes) {
+        cudaStreamSynchronize(h->stream);
+        if (h->adj_lam) cudaFree(h->adj_lam);
+        h->adj_lam = nullptr;
+        h->adj_lam_bytes = 0;
+        if (cudaMalloc(&h->adj_lam, lam_bytes) != cudaSuccess) {
+            h->adj_lam = nullptr;
+            *msg = "adjoint cotangent staging allocation failed";
+            return TSLB_ERR_ALLOC;
+        }
+        h->adj_lam_bytes = lam_bytes;
+    }
     cudaError_t e = cudaSuccess;
     if (h->adj_ws_bytes < need) {
         cudaStreamSynchronize(h->stream);
@@ -479,8 +525,13 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
     auto cleanup = [&]() { cudaStreamSynchronize(h->stream); };
     Physics p = make_physics(h);
     e = cudaMemsetAsync(fbar, 0, sizeof(float) * 3 * fs, h->stream);
+    const double* lam_dev = lambda;
+    if (lambda && where == TSLB_HOST && e == cudaSuccess) {
+        e = cudaMemcpyAsync(h->adj_lam, lambda, lam_bytes, cudaMemcpyHostToDevice, h->stream);
+        lam_dev = static_cast<const double*>(h->adj_lam);
+    }
     int cur = 0;
-    if (e == cudaSuccess) e = adj_launch(h, 0, h->buf[h->cur], nullptr, gbar[cur], nullptr, p);
+    if (e == cudaSuccess) e = adj_launch(h, 0, h->buf[h->cur], lam_dev, gbar[cur], nullptr, p);
     int64_t n_end = h->t;
     const int64_t n_stop = h->t - nsteps;
     while (e == cudaSuccess && n_end > n_stop) {
@@ -507,7 +558,7 @@ int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, st
     // scatter the interior gradient into the full-lattice [3][N] output; with
     // y walls its interior rows 1 .. ny - 2 of each z plane, the wall layers 0
     if (e == cudaSuccess) {
-        const long long fnx = h->dims[0], fny = h->dims[1], fN = fnx * fny * h->dims[2];
+        const long long fnx = h->dims[0], fny = h->dims[1];
         const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
         if (!ywalls) {
             for (int a = 0; a < 3 && e == cudaSuccess; ++a)

@@ -97,6 +97,7 @@ void release(tslb_s* h) {
     if (h->diag_host) cudaFreeHost(h->diag_host);
     for (void* c : h->ckpts) cudaFree(c);
     if (h->adj_ws) cudaFree(h->adj_ws);
+    if (h->adj_lam) cudaFree(h->adj_lam);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -580,8 +581,8 @@ int tslb_diagnostics(tslb_t* h, tslb_diag* out) {
     return TSLB_OK;
 }
 
-int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where) {
-    const Range range("tslb_adjoint_force_gradient");
+// Checks shared by the two adjoint entry points, then the sweep.
+static int adjoint_common(tslb_t* h, const double* lambda, int64_t nsteps, float* dJdF, int where) {
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (!dJdF) return fail(h, TSLB_ERR_INVALID, "null output");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
@@ -590,9 +591,23 @@ int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int wher
     if (h->forcing != TSLB_FORCING_LUO) return fail(h, TSLB_ERR_UNSUPPORTED, "the adjoint is implemented for Luo forcing");
     cudaSetDevice(h->device);
     std::string msg;
-    const int r = tslb::adjoint_force_gradient(h, nsteps, dJdF, where, &msg);
+    const int r = tslb::adjoint_run(h, lambda, nsteps, dJdF, where, &msg);
     if (r != TSLB_OK) return fail(h, r, msg);
     return TSLB_OK;
+}
+
+int tslb_adjoint_force_gradient(tslb_t* h, int64_t nsteps, float* dJdF, int where) {
+    const Range range("tslb_adjoint_force_gradient");
+    return adjoint_common(h, nullptr, nsteps, dJdF, where);
+}
+
+int tslb_adjoint(tslb_t* h, const double* lambda_T, int64_t nsteps, int ckpt_every, float* dJdF, int where) {
+    const Range range("tslb_adjoint");
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (!lambda_T) return fail(h, TSLB_ERR_INVALID, "null cotangent");
+    if (ckpt_every != 0 && ckpt_every != h->checkpoint_every)
+        return fail(h, TSLB_ERR_INVALID, "ckpt_every must be 0 or the handle's checkpoint_every");
+    return adjoint_common(h, lambda_T, nsteps, dJdF, where);
 }
 
 int64_t tslb_interior_nodes(const tslb_t* h) { return h ? (int64_t)h->g.plane * h->g.nz : 0; }

@@ -552,6 +552,10 @@ struct tslb_s {
     // tslb_destroy: adj_ws_bytes bytes at adj_ws
     void* adj_ws = nullptr;
     size_t adj_ws_bytes = 0;
+    // device copy of a host cotangent for tslb_adjoint (FP64 [10][N]), kept
+    // from its first use until tslb_destroy
+    void* adj_lam = nullptr;
+    size_t adj_lam_bytes = 0;
     std::string err;
 };
 
@@ -568,7 +572,7 @@ cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, co
 // The step kernel tslb_step uses for this handle (same choice, bitwise-identical results).
 cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p);
 bool use_factored(const tslb_s* h);
-int adjoint_force_gradient(tslb_s* h, int64_t nsteps, float* dJdF, int where, std::string* msg);
+int adjoint_run(tslb_s* h, const double* lambda, int64_t nsteps, float* dJdF, int where, std::string* msg);
 bool factored_supports(const tslb_s* h);
 cudaError_t launch_encode(const tslb_s* h, const double* rho, const double* u, const double* pi, void* dst,
                           const Physics& p);

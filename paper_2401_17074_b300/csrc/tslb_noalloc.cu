@@ -3,8 +3,11 @@
 // Same FP64 sums as tslb_diagnostics, but over moment arrays the caller
 // owns (the full-lattice FP64 layout that tslb_get_moments writes) and with
 // the per-block partial sums kept in a fixed file-scope device array instead
-// of memory obtained from cudaMalloc.  For callers that may not allocate
-// device memory at the point where they want the numbers.
+// of memory obtained from cudaMalloc.  For callers that cannot allocate
+// device memory where they want the numbers: a fixed device-memory budget
+// that is already spent, a framework allocator that owns every byte of the
+// device, or a latency-bound loop in which cudaMalloc / cudaFree (which may
+// synchronise the device) are not acceptable.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -26,7 +29,11 @@ static_assert(NA_NODES_PER_BLOCK * NA_MAX_BLOCKS == TSLB_NOALLOC_MAX_NODES, "lim
 // slot has to start at zero; two calls that overlap on the GPU race here.
 static __device__ __align__(256) double g_noalloc_partials[NA_MAX_BLOCKS * NA_SUMS];
 
-// Host-side device address of g_noalloc_partials, looked up once per device.
+// Host-side device address of g_noalloc_partials, looked up once per device
+// (on the first call with that device current) and kept for the life of the
+// process.  It belongs to the device's primary context: after cudaDeviceReset
+// on that device the cached address is stale and this entry point must not be
+// called again in the process.
 std::mutex g_mu;
 double* g_partials_addr[64] = {};
 
@@ -50,8 +57,16 @@ __global__ void __launch_bounds__(NA_THREADS) noalloc_partial_kernel(const doubl
         const long long xi = n % nx, yi = (n / nx) % ny, zi = n / (nx * ny);
         const long long node = (xi + lo0) + fnx * ((yi + lo1) + fny * (zi + lo2));
         const double r = rho[node], ux = u[node], uy = u[fN + node], uz = u[2 * fN + node];
-        const double pxy = pi ? pi[3 * fN + node] : 0.0;
-        if (!(isfinite(r) && isfinite(ux) && isfinite(uy) && isfinite(uz) && isfinite(pxy))) {
+        // a node counts as non-finite if any of its ten moments is NaN or Inf,
+        // as in tslb_diagnostics
+        bool finite = isfinite(r) && isfinite(ux) && isfinite(uy) && isfinite(uz);
+        double pxy = 0.0;
+        if (pi) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) finite = finite && isfinite(pi[k * fN + node]);
+            pxy = pi[3 * fN + node];
+        }
+        if (!finite) {
             acc[7] += 1.0;
             continue;
         }
@@ -116,9 +131,11 @@ extern "C" int tslb_diagnostics_noalloc(const double* rho, const double* u, cons
         lo[a] = per ? 0 : 1;
         ext[a] = per ? dims[a] : dims[a] - 2;
     }
-    const long long total = ext[0] * ext[1] * ext[2];
-    if (total > TSLB_NOALLOC_MAX_NODES)
+    // the interior count, checked factor by factor so the product cannot overflow
+    const long long lim = TSLB_NOALLOC_MAX_NODES;
+    if (ext[0] > lim || ext[1] > lim / ext[0] || ext[2] > lim / (ext[0] * ext[1]))
         return na_fail(TSLB_ERR_INVALID, "more interior nodes than TSLB_NOALLOC_MAX_NODES (2^26); use tslb_diagnostics");
+    const long long total = ext[0] * ext[1] * ext[2];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(TSLB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));

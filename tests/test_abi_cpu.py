@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "tslb.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(tslb_[a-z_]+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(tslb_[a-z0-9_]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -156,3 +156,23 @@ def test_null_handle_calls_fail_cleanly():
     assert L.tslb_synchronize(None) == T.TSLB_ERR_INVALID
     assert L.tslb_interior_nodes(None) == 0
     L.tslb_destroy(None)
+    assert L.tslb_adjoint(None, None, 4, 0, None, T.HOST) == T.TSLB_ERR_INVALID
+    assert L.tslb_adjoint_force_gradient(None, 4, None, T.HOST) == T.TSLB_ERR_INVALID
+
+
+def test_noalloc_wrapper_rejects_bad_arrays_before_launch():
+    """The binding checks the device, dtype, layout and length of every array
+    the no-allocation kernels read or write before it calls the library, so a
+    short, CPU or float32 array never reaches a launch (these run without a
+    GPU: each case is rejected in Python)."""
+    import torch
+    dims, bc = (4, 4, 4), (0,) * 6
+    N = 64
+    cpu = torch.zeros(N, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        T.tslb_diagnostics_noalloc(cpu, torch.zeros(3 * N, dtype=torch.float64), None, dims, bc, 0.6,
+                                   torch.zeros(8, dtype=torch.float64))
+    with pytest.raises(ValueError, match="dims"):
+        T.tslb_diagnostics_noalloc(cpu, cpu, None, (4, 4), bc, 0.6, cpu)
+    with pytest.raises(ValueError, match="out must be given"):
+        T.tslb_diagnostics_noalloc(cpu, cpu, None, dims, bc, 0.6, None)

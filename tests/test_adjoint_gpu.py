@@ -298,3 +298,122 @@ def test_autograd_function(cuda_ok):
     rho, u, _ = s.get_moments()
     assert abs(J.item() - 0.5 * np.sum(rho * (u ** 2).sum(0))) < 1e-9
     s.close()
+
+
+def _profile_weights(dims, seed):
+    """Random weights w_y of the plane-averaged u_x(y) profile over the interior rows."""
+    w = np.random.default_rng(seed).standard_normal(dims[1])
+    return w
+
+
+def _objective_np(dims, bc, w, W10, rho, u, pi):
+    """J(m) on (possibly complex) full-lattice moments, numpy: the u_x(y)
+    profile averaged over x and z and weighted by w, plus sum W10 . m over all
+    ten fields, plus 1/2 sum rho u_y^2.  Holomorphic (no conjugates), so the
+    complex step differentiates it."""
+    nx, ny, nz = dims
+    ux = u[0].reshape(nz, ny, nx)
+    prof = ux.mean(axis=(0, 2))
+    y0, y1 = (1, ny - 1) if bc[2] != 0 else (0, ny)
+    J = np.sum(w[y0:y1] * prof[y0:y1])
+    m = np.concatenate([rho.reshape(1, -1), u, pi], axis=0)
+    J = J + np.sum(W10 * m) + 0.5 * np.sum(rho * u[1] ** 2)
+    return J
+
+
+def _objective_torch(dims, bc, w, W10, rho, u, pi):
+    import torch
+    nx, ny, nz = dims
+    prof = u[0].view(nz, ny, nx).mean(dim=(0, 2))
+    y0, y1 = (1, ny - 1) if bc[2] != 0 else (0, ny)
+    wt = torch.as_tensor(w, dtype=torch.float64, device=u.device)
+    J = torch.sum(wt[y0:y1] * prof[y0:y1])
+    m = torch.cat([rho.view(1, -1), u, pi], dim=0)
+    J = J + torch.sum(torch.as_tensor(W10, device=u.device) * m) + 0.5 * torch.sum(rho * u[1] ** 2)
+    return J
+
+
+@pytest.mark.parametrize("case", ["periodic16", "channel"])
+def test_adjoint_general_objective(cuda_ok, case):
+    """A second objective through tslb_adjoint and the autograd Function that
+    returns the final moments: the plane-averaged u_x(y) profile weighted by a
+    random vector, plus a random linear functional of all ten moment fields,
+    plus 1/2 sum rho u_y^2.  torch builds the cotangent of the final moments;
+    the library's adjoint maps it to dJ/dF.  Directional derivatives must
+    agree with the oracle's complex step of the same objective to 1e-4
+    relative, on a 16^3 periodic box (64 steps, checkpoints every 16) and on a
+    40 x 10 x 6 channel box with bounce-back y walls (12 steps, every 4)."""
+    import torch
+    from paper_2401_17074_b300.autograd import final_moments
+    if case == "periodic16":
+        n, nsteps, tau, k, bc = 16, 64, 0.52, 16, (0,) * 6
+        dims, state = W.divfree_random(n=n, u_rms=0.02, kmax=5, tau=tau, seed=5)
+    else:
+        dims, tau, nsteps, k, bc = (40, 10, 6), 0.6, 12, 4, (0, 0, 1, 1, 0, 0)
+        state = W.random_state(dims, seed=44, drho=0.002, du=0.02, dpi=1e-4)
+    N = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(91)
+    w = _profile_weights(dims, 92)
+    W10 = 1e-3 * rng.standard_normal((10, N))
+    F0 = (1e-5 * rng.uniform(-1, 1, (3, N))).astype(np.float32)
+    s = T.Solver(dims, tau, bc=bc, checkpoint_every=k)
+    F = torch.tensor(F0, device="cuda", requires_grad=True)
+    rho, u, pi = final_moments(F, s, state, nsteps)
+    J = _objective_torch(dims, bc, w, W10, rho, u, pi)
+    J.backward()
+    g = F.grad.detach().cpu().numpy().astype(np.float64)
+    s.close()
+    # the forward value against the oracle's real run of the same objective
+    r0, u0, p0 = oracle.complex_step_moments(dims, tau, bc, state[0], state[1], state[2], F0.astype(np.float64),
+                                             np.zeros((3, N)), nsteps)
+    J_or = _objective_np(dims, bc, w, W10, r0, u0, p0).real
+    assert abs(J.item() - J_or) <= 1e-5 * (abs(J_or) + 1e-3)
+    for trial in range(2):
+        v = rng.standard_normal((3, N))
+        h = 1e-30
+        rc, uc, pc = oracle.complex_step_moments(dims, tau, bc, state[0], state[1], state[2], F0.astype(np.float64),
+                                                 h * v, nsteps)
+        d_cs = _objective_np(dims, bc, w, W10, rc, uc, pc).imag / h
+        d_adj = float(np.sum(g * v))
+        assert abs(d_adj - d_cs) <= 1e-4 * abs(d_cs), (trial, d_adj, d_cs)
+
+
+def test_adjoint_cotangent_reproduces_kinetic_energy_seed(cuda_ok):
+    """tslb_adjoint with the cotangent of J = 1/2 sum rho |u|^2, that is
+    (|u|^2 / 2, rho u, 0) built on the host from the final moments, gives the
+    gradient of tslb_adjoint_force_gradient (the seed on the device) up to the
+    FP32 rounding of the seed: 1e-6 relative in L2.  Also from device arrays."""
+    import torch
+    n, nsteps = 8, 32
+    dims, state, s = _setup(n, nsteps=nsteps)
+    N = n ** 3
+    s.init_moments(*state)
+    s.set_force_field(np.zeros((3, N), dtype=np.float32))
+    s.step(nsteps)
+    g_ke = s.adjoint_force_gradient(nsteps).astype(np.float64)
+    rho, u, pi = s.get_moments()
+    lam = np.concatenate([0.5 * (u ** 2).sum(0), (rho * u).reshape(-1), np.zeros(6 * N)])
+    g_host = s.adjoint(lam, nsteps).astype(np.float64)
+    lam_d = torch.tensor(lam, device="cuda")
+    g_dev = torch.empty((3, N), dtype=torch.float32, device="cuda")
+    T.tslb_adjoint(s.handle, lam_d, nsteps, 16, g_dev, T.DEVICE)
+    s.close()
+    assert np.linalg.norm(g_host - g_ke) <= 1e-6 * np.linalg.norm(g_ke)
+    assert np.array_equal(g_dev.cpu().numpy(), g_host.astype(np.float32))
+
+
+def test_adjoint_cotangent_errors(cuda_ok):
+    n = 8
+    dims, state, s = _setup(n)
+    N = n ** 3
+    s.init_moments(*state)
+    s.set_force_field(np.zeros((3, N), dtype=np.float32))
+    s.step(16)
+    lam = np.zeros(10 * N)
+    g = np.zeros(3 * N, dtype=np.float32)
+    with pytest.raises(T.TslbError) as ei:
+        T.tslb_adjoint(s.handle, lam, 16, 8, g, T.HOST)  # not the handle's checkpoint interval
+    assert ei.value.code == T.TSLB_ERR_INVALID
+    T.tslb_adjoint(s.handle, lam, 16, 16, g, T.HOST)
+    assert np.all(g == 0)  # a zero cotangent has a zero gradient
+    s.close()

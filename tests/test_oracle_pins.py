@@ -561,3 +561,258 @@ def test_complex_step_matches_central_differences():
     d_fd = (Jp - Jm) / (2 * eps)
     assert abs(J.real - _energy_real(dims, tau, rho, u, pi, F0, nsteps)) < 1e-14
     assert abs(d_cs - d_fd) / abs(d_cs) < 1e-6
+
+
+# ---- the inflow and outflow ghost layers (Sec. 2.3, Sec. 3.2) -----------------
+#
+# An independent restatement of the third-order Hermite populations in
+# explicit components, written for these pins (the oracle sums the full
+# alpha, beta, gamma tensors):  on D3Q27 the xxx-type H3 vanish (c^3 = c), the
+# three orderings of an aab index set share H_aab = (c_a^2 - cs^2) c_b and the
+# six orderings of xyz share c_x c_y c_z, so
+#   (1/6cs^6) H3 : T = (1/2cs^6) sum_{a != b} (c_a^2 - cs^2) c_b T_aab + (1/cs^6) c_x c_y c_z T_xyz.
+
+def _h3_sum(c, T_aab, T_xyz):
+    s = 0.0
+    for a in range(3):
+        for b in range(3):
+            if a != b:
+                s += (c[a] * c[a] - CS2) * c[b] * T_aab(a, b)
+    return s / (2 * CS2 ** 3) + c[0] * c[1] * c[2] * T_xyz / CS2 ** 3
+
+
+def _feq_np(rho, u, c, w):
+    out = np.zeros(27)
+    for i in range(27):
+        cu = float(np.dot(c[i], u))
+        h2 = (cu * cu - CS2 * float(np.dot(u, u))) / (2 * CS2 * CS2)
+        h3 = _h3_sum(c[i], lambda a, b: u[a] * u[a] * u[b], u[0] * u[1] * u[2])
+        out[i] = w[i] * rho * (1.0 + cu / CS2 + h2 + h3)
+    return out
+
+
+def _fneq_np(P, u, c, w):
+    out = np.zeros(27)
+    for i in range(27):
+        ci = c[i]
+        h2 = sum((ci[a] * ci[b] - CS2 * (a == b)) * P[a, b] for a in range(3) for b in range(3)) / (2 * CS2 * CS2)
+        h3 = _h3_sum(ci, lambda a, b: 2 * P[a, b] * u[a] + P[a, a] * u[b],
+                     P[0, 1] * u[2] + P[1, 2] * u[0] + P[0, 2] * u[1])
+        out[i] = w[i] * (h2 + h3)
+    return out
+
+
+def _jet_box(noise_amp=0.01):
+    dims = (8, 7, 6)
+    inflow = dict(center2=(7, 6), diameter=5, u_jet=0.05, noise_amp=noise_amp, seed=21)
+    return dims, inflow
+
+
+def _inside_nozzle(inflow, X, Y):
+    dx, dy = 2 * X - inflow["center2"][0], 2 * Y - inflow["center2"][1]
+    return dx * dx + dy * dy <= inflow["diameter"] ** 2
+
+
+def _entering_ghost_check(s, dims, inflow, tau, pops_F, rhoF, uF, t, hermite):
+    """Step the oracle once from time t and compare the nine populations that
+    enter each first-layer node (x, y, 1) from the inflow ghost with Eq.
+    neq_final_guo: f^eq(rho_B = rho(x_F), u_B) + (1 - omega) f^neq(x_F), where
+    x_F = (x - c_x, y - c_y, 1) is the fluid neighbour of the emitting ghost
+    node.  f^neq(x_F) is the population form f(x_F) - f^eq(x_F) (pops_F given)
+    or, with `hermite`, the Hermite f^neq of x_F's moments (Eq. neq_final)."""
+    c, w = oracle.lattice()
+    nx, ny, nz = dims
+    omega = 1.0 / tau
+    s.step(1)
+    f1 = s.get_populations()
+    worst, n = 0.0, 0
+    for y in range(ny):
+        for x in range(nx):
+            dest = x + nx * (y + ny * 1)
+            for i in range(27):
+                if c[i][2] != 1:
+                    continue
+                X, Y = (x - c[i][0]) % nx, (y - c[i][1]) % ny  # periodic x, y
+                nF = X + nx * (Y + ny * 1)
+                uB = np.zeros(3)
+                if _inside_nozzle(inflow, X, Y):
+                    xi = oracle.inflow_noise(inflow["seed"], X, Y, t)
+                    uB[2] = inflow["u_jet"] * (1.0 + inflow["noise_amp"] * xi)
+                if hermite is None:
+                    neq = pops_F[nF] - _feq_np(rhoF[nF], uF[:, nF], c, w)
+                else:
+                    neq = _fneq_np(hermite[nF], uF[:, nF], c, w)
+                want = _feq_np(rhoF[nF], uB, c, w)[i] + (1.0 - omega) * neq[i]
+                worst = max(worst, abs(f1[dest, i] - want))
+                n += 1
+    return worst, n
+
+
+def test_inflow_ghost_population_form_at_start():
+    """Eq. neq_final_guo in population form on a sheared, non-uniform state:
+    random rho, u and Pi^neq at every node (so u(x_F) != u_B and Pi != 0),
+    periodic x and y, a nozzle that covers part of the face, 1 % noise.  At
+    t = 0 the populations are the regularised ones built from the moments, so
+    f(x_F) - f^eq(x_F) is exactly the Hermite f^neq of Eq. neq_final and the
+    two forms coincide: every entering population must match to 1e-13.  A
+    ghost that took u_B inside f^neq, Pi of the ghost node, rho of another
+    node or dropped (1 - omega) fails."""
+    dims, inflow = _jet_box()
+    tau = 0.6
+    N = dims[0] * dims[1] * dims[2]
+    rho, u, pi = W.random_state(dims, seed=61, drho=0.02, du=0.04, dpi=2e-3)
+    s = oracle.OracleSim(dims, tau, bc=(0, 0, 0, 0, 3, 4), inflow=inflow)
+    s.init_moments(rho, u, pi)
+    f0 = s.get_populations()
+    u = np.asarray(u).reshape(3, N)
+    worst, n = _entering_ghost_check(s, dims, inflow, tau, f0, np.asarray(rho).reshape(-1), u, 0, None)
+    assert n == 9 * dims[0] * dims[1]
+    assert worst < 1e-13, worst
+    # the nozzle covers some columns but not all, so both branches were taken
+    cols = [_inside_nozzle(inflow, X, Y) for X in range(dims[0]) for Y in range(dims[1])]
+    assert any(cols) and not all(cols)
+
+
+def test_inflow_ghost_hermite_form_later_step():
+    """Eq. neq_final after three steps: the populations entering z = 1 equal
+    f^eq(rho(x_F), u_B) + (1 - omega) times the Hermite f^neq of Pi^neq(x_F)
+    and u(x_F), with x_F's moments read back from the oracle at t = 3 and the
+    noise drawn for t = 3 (to 1e-13).  Here f(x_F) is no longer in regularised
+    form, so the population-form difference would not match: the check tells
+    Eq. neq_final from Eq. neq_final_guo."""
+    dims, inflow = _jet_box()
+    tau = 0.7
+    N = dims[0] * dims[1] * dims[2]
+    state = W.random_state(dims, seed=62, drho=0.02, du=0.04, dpi=2e-3)
+    s = oracle.OracleSim(dims, tau, bc=(0, 0, 0, 0, 3, 4), inflow=inflow)
+    s.init_moments(*state)
+    s.step(3)
+    rho, u, pi = s.get_moments()
+    P = np.array([_sym(pi[:, k]) for k in range(N)])
+    worst, n = _entering_ghost_check(s, dims, inflow, tau, None, rho, u, 3, P)
+    assert worst < 1e-13, worst
+    # and the population-form difference does not coincide any more
+    s2 = oracle.OracleSim(dims, tau, bc=(0, 0, 0, 0, 3, 4), inflow=inflow)
+    s2.init_moments(*state)
+    s2.step(3)
+    f3 = s2.get_populations()
+    worst_pop, _ = _entering_ghost_check(s2, dims, inflow, tau, f3, rho, u, 3, None)
+    assert worst_pop > 1e-9
+
+
+def test_outflow_ghost_copies_last_layer():
+    """The zero-gradient outflow (Sec. 3.2): the ghost layer z = nz - 1 emits the
+    post-collision populations of the moments of z = nz - 2.  On a state that
+    is linear in z (so every layer differs), the nine populations entering each
+    node of z = nz - 2 from the ghost after one step must equal the explicit
+    f^eq + (1 - omega) f^neq + Luo force term of the moments at
+    (x - c_x, y - c_y, nz - 2), to 1e-13; a copy from z = nz - 3 would differ
+    by one layer's slope."""
+    dims, inflow = _jet_box(noise_amp=0.0)
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    tau, F = 0.65, np.array([1e-5, -2e-5, 3e-5])
+    z = np.repeat(np.arange(nz), nx * ny).astype(float)
+    base = W.random_state(dims, seed=63, drho=0.005, du=0.01, dpi=5e-4)
+    rho = np.asarray(base[0]).reshape(-1) + 0.01 * z
+    u = np.asarray(base[1]).reshape(3, N) + np.array([0.004, -0.003, 0.005])[:, None] * z
+    pi = np.asarray(base[2]).reshape(6, N) + 2e-4 * z
+    s = oracle.OracleSim(dims, tau, force=F, bc=(0, 0, 0, 0, 3, 4), inflow=inflow)
+    s.init_moments(rho, u, pi)
+    s.step(1)
+    f1 = s.get_populations()
+    c, w = oracle.lattice()
+    omega = 1.0 / tau
+    worst = 0.0
+    for y in range(ny):
+        for x in range(nx):
+            dest = x + nx * (y + ny * (nz - 2))
+            for i in range(27):
+                if c[i][2] != -1:
+                    continue
+                X, Y = (x - c[i][0]) % nx, (y - c[i][1]) % ny
+                src = X + nx * (Y + ny * (nz - 2))  # the layer the ghost copies
+                P = _sym(pi[:, src])
+                want = (_feq_np(rho[src], u[:, src], c, w)[i] + (1 - omega) * _fneq_np(P, u[:, src], c, w)[i]
+                        + rho[src] * w[i] * float(np.dot(c[i], F)) / CS2)
+                worst = max(worst, abs(f1[dest, i] - want))
+    assert worst < 1e-13, worst
+
+
+def test_outflow_ghost_follows_last_layer_over_time():
+    """After several steps the ghost still copies the current z = nz - 2 layer:
+    the populations entering z = nz - 2 at step t + 1 are those rebuilt from
+    that layer's moments at step t (read back from the oracle)."""
+    dims, inflow = _jet_box()
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    tau = 0.6
+    s = oracle.OracleSim(dims, tau, bc=(0, 0, 0, 0, 3, 4), inflow=inflow)
+    s.init_moments(*W.random_state(dims, seed=64, drho=0.01, du=0.03, dpi=1e-3))
+    s.step(4)
+    rho, u, pi = s.get_moments()
+    s.step(1)
+    f1 = s.get_populations()
+    c, w = oracle.lattice()
+    omega = 1.0 / tau
+    worst = 0.0
+    for y in range(ny):
+        for x in range(nx):
+            dest = x + nx * (y + ny * (nz - 2))
+            for i in range(27):
+                if c[i][2] != -1:
+                    continue
+                src = (x - c[i][0]) % nx + nx * ((y - c[i][1]) % ny + ny * (nz - 2))
+                want = (_feq_np(rho[src], u[:, src], c, w)[i]
+                        + (1 - omega) * _fneq_np(_sym(pi[:, src]), u[:, src], c, w)[i])
+                worst = max(worst, abs(f1[dest, i] - want))
+    assert worst < 1e-13, worst
+
+
+def test_explicit_hermite_restatement_matches_moment_identities(lat):
+    """The explicit-component restatement used by the ghost pins above is
+    itself held to the defining moments: f^eq has mass rho, momentum rho u and
+    second moment rho u u + rho cs^2 delta; f^neq has zero mass and momentum
+    and second moment Pi (random states)."""
+    c, w = lat
+    rng = np.random.default_rng(65)
+    for _ in range(5):
+        rho, u = 1 + 0.05 * rng.uniform(-1, 1), 0.08 * rng.uniform(-1, 1, 3)
+        P = _sym(1e-3 * rng.uniform(-1, 1, 6))
+        fe, fn = _feq_np(rho, u, c, w), _fneq_np(P, u, c, w)
+        cc = c.astype(float)
+        assert abs(fe.sum() - rho) < 1e-15 and np.abs(cc.T @ fe - rho * u).max() < 1e-15
+        assert np.abs(np.einsum("i,ia,ib->ab", fe, cc, cc) - (rho * np.outer(u, u) + rho * CS2 * np.eye(3))).max() < 1e-15
+        assert abs(fn.sum()) < 1e-16 and np.abs(cc.T @ fn).max() < 1e-16
+        assert np.abs(np.einsum("i,ia,ib->ab", fn, cc, cc) - P).max() < 1e-16
+
+
+def test_poiseuille_stress_closed_form():
+    """Steady Poiseuille flow between halfway bounce-back walls: the momentum
+    balance fixes the shear stress, sigma_xy(y) = rho g (y_c - y) with y_c the
+    channel centre, and the viscous stress of the regularised scheme is
+    -(1 - omega/2) Pi^neq_xy.  At every fluid row the oracle's stress must match
+    to 1e-9 relative to its wall value rho g (H - 1/2) (a sign or factor
+    error in Pi^neq, or in the (1 - omega) relaxation, fails)."""
+    H2, tau, g = 16, 0.8, 1e-6
+    ny = H2 + 2
+    dims = (3, ny, 3)
+    N = 3 * ny * 3
+    nu = CS2 * (tau - 0.5)
+    y = np.tile(np.repeat(np.arange(ny, dtype=float), 3), 3)
+    y0, y1 = 0.5, ny - 1.5
+    fluid = (y >= 1) & (y <= ny - 2)
+    u = np.zeros((3, N))
+    u[0] = np.where(fluid, g / (2 * nu) * (y - y0) * (y1 - y), 0.0)
+    pi = np.zeros((6, N))
+    s = oracle.OracleSim(dims, tau, force=(g, 0, 0), bc=(0, 0, 1, 1, 0, 0))
+    s.init_moments(np.ones(N), u, pi)
+    s.step(int(3 * H2 * H2 / nu))
+    rho, _, p = s.get_moments()
+    sc = 1.0 - 0.5 / tau
+    yc = 0.5 * (y0 + y1)
+    wall = g * (0.5 * (y1 - y0) - 0.5)
+    for j in range(1, ny - 1):
+        m = y == j
+        stress = float(np.mean(-sc * p[3][m]))
+        assert abs(stress - float(np.mean(rho[m])) * g * (yc - j)) <= 1e-9 * wall, j

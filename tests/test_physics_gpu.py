@@ -107,3 +107,52 @@ def test_resume_from_saved_moments(cuda_ok, prec):
     b.close()
     for x, y in zip(got, ref):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("kernel", [T.KERNEL_FACTORED, T.KERNEL_DIRECT], ids=["factored", "direct"])
+def test_wall_shear_diagnostic_poiseuille(cuda_ok, kernel):
+    """The wall-shear diagnostic against the closed form: in steady Poiseuille
+    flow between halfway bounce-back walls the shear stress is linear,
+    sigma_xy(y) = rho g (y_c - y), so at the wall-adjacent nodes (half a node
+    from the walls) the diagnostic -(1 - omega/2) Pi_xy must read
+    rho g (H - 1/2) with H the half-width.  The regularised scheme reproduces
+    the linear stress exactly (the oracle: 1e-12); the bound 1e-4 covers the
+    FP32 storage of Pi^neq and the remaining transient (8 H^2 / nu steps)."""
+    H, tau = 8, 0.8
+    nu = CS2 * (tau - 0.5)
+    g = 0.01 * 8 * nu / (2 * H) ** 2
+    ny = 2 * H + 2
+    dims = (4, ny, 4)
+    N = dims[0] * dims[1] * dims[2]
+    s = T.Solver(dims, tau, force=(g, 0.0, 0.0), bc=(0, 0, 1, 1, 0, 0), kernel=kernel)
+    s.init_moments(np.ones(N), np.zeros((3, N)), np.zeros((6, N)))
+    s.step(int(8 * (2 * H) ** 2 / nu))
+    d, code = s.diagnostics()
+    rho, _, _ = s.get_moments()
+    s.close()
+    assert code == T.TSLB_OK
+    fluid = ((np.arange(N) // dims[0]) % ny >= 1) & ((np.arange(N) // dims[0]) % ny <= ny - 2)
+    want = float(rho[fluid].mean()) * g * (H - 0.5)
+    assert abs(d["wall_shear"] / want - 1) < 1e-4, (d["wall_shear"], want)
+
+
+def test_wall_shear_diagnostic_numpy_sum(cuda_ok):
+    """On a walled box in a non-trivial state (random moments, eleven steps),
+    tslb_diagnostics' FP64 wall shear equals the mean of -(1 - omega/2) Pi_xy
+    over the nodes of y = 1 and of +(1 - omega/2) Pi_xy over y = ny - 2,
+    summed in numpy from the moments read back (1e-12 relative); with NEE walls
+    the same rows count."""
+    for bcy in (1, T.NEE_WALL):
+        dims, tau = (13, 9, 7), 0.57
+        N = dims[0] * dims[1] * dims[2]
+        s = T.Solver(dims, tau, force=(1e-5, 0.0, 0.0), bc=(0, 0, bcy, bcy, 0, 0))
+        s.init_moments(*W.random_state(dims, seed=71, drho=0.005, du=0.02, dpi=1e-3))
+        s.step(11)
+        d, code = s.diagnostics()
+        _, _, pi = s.get_moments()
+        s.close()
+        assert code == T.TSLB_OK
+        y = (np.arange(N) // dims[0]) % dims[1]
+        sc = 1.0 - 0.5 / tau
+        want = (np.sum(-sc * pi[3][y == 1]) + np.sum(sc * pi[3][y == dims[1] - 2])) / (2 * dims[0] * dims[2])
+        assert abs(d["wall_shear"] - want) <= 1e-12 * abs(want), (bcy, d["wall_shear"], want)
