@@ -76,6 +76,14 @@ typedef enum tslb_bc {
     TSLB_BC_FREESLIP = 2,   /* halfway specular-reflection wall (x or y faces) */
     TSLB_BC_INFLOW = 3,     /* z- only: thread-safe Hermite non-equilibrium inflow, Eq. neq_final */
     TSLB_BC_OUTFLOW = 4,    /* z+ only: zero-gradient outflow (moments of the adjacent layer) */
+    TSLB_BC_HALO = 6,       /* z faces only, both: this handle is one z slab of a larger lattice split along
+                               z (the multi-GPU decomposition named as future work in the paper's
+                               Conclusions).  Every node layer z = 0 .. nz-1 is interior; the step reads the
+                               layers z = -1 and z = nz from two ghost planes, which the caller fills
+                               between steps with the neighbouring slabs' boundary layers
+                               (tslb_halo_export / tslb_halo_import).  D3Q27, factored kernel, periodic
+                               x, periodic or bounce-back y, Luo forcing with the constant body force only
+                               (no force field, sponge, checkpoints or adjoint) */
     TSLB_BC_NEE_WALL = 5    /* y faces only, with periodic x and z: no-slip wall on the boundary layer by
                                the thread-safe non-equilibrium extrapolation (Sec. 2.3, Eq. neq_final with
                                imposed momentum u_B = 0): each boundary node emits
@@ -301,6 +309,36 @@ int tslb_adjoint(tslb_t* h, const double* lambda_T, int64_t nsteps, int ckpt_eve
 #define TSLB_NOALLOC_MAX_NODES ((int64_t)1 << 26)
 int tslb_diagnostics_noalloc(const double* rho, const double* u, const double* pi, const int64_t dims[3],
                              const int bc[6], double tau, void* stream, double* out);
+
+/* ---- Slab decomposition along z (TSLB_BC_HALO faces) --------------------
+ * The paper's Conclusions name the multi-GPU extension as future work; its
+ * natural form for the thread-safe step is a split of the lattice into z
+ * slabs, one handle per slab, whose steps need one layer of the 10 stored
+ * moment fields from each neighbour per time step.  A packed plane holds the
+ * nx * ny interior nodes of one layer as the three stored arrays in turn
+ * (V0 = (u_x, u_y, u_z, rho - 1), V1 = (Pi_xx, Pi_yy, Pi_zz, Pi_xy),
+ * V2 = (Pi_xz, Pi_yz)), in the handle's storage type: 10 * nx * ny values.
+ * One exchange per step, before it: for each slab s,
+ *   tslb_halo_export(s, 1, buf)  ->  tslb_halo_import(next slab, 0, buf)
+ *   tslb_halo_export(s, 0, buf)  ->  tslb_halo_import(previous slab, 1, buf)
+ * with the slabs in a ring (z periodic overall).  Both calls run on the
+ * handle's stream (device buffers) or complete before returning (host
+ * buffers); a device buffer shared by two handles on different streams must
+ * be ordered between them by the caller (an event, or one shared stream).
+ * All three return TSLB_ERR_STATE on a handle without TSLB_BC_HALO faces. */
+
+/* Bytes of one packed plane. */
+int tslb_halo_plane_bytes(const tslb_t* h, int64_t* bytes);
+
+/* Copy this slab's boundary layer -- side 0: z = 0, side 1: z = nz - 1, at the
+ * current step -- into dst as one packed plane (host or device per `where`). */
+int tslb_halo_export(tslb_t* h, int side, void* dst, int where);
+
+/* Load a packed plane into the ghost plane the next step reads -- side 0: the
+ * layer below z = 0 (the previous slab's z = nz - 1), side 1: the layer above
+ * z = nz - 1 (the next slab's z = 0).  The ghost planes start at the rest
+ * state and keep their contents until the next import. */
+int tslb_halo_import(tslb_t* h, int side, const void* src, int where);
 
 /* Number of interior (updated) nodes. */
 int64_t tslb_interior_nodes(const tslb_t* h);

@@ -23,7 +23,7 @@ TSLB_ERR_STATE = -6
 
 TSLB_D3Q27 = 27
 TSLB_D2Q9 = 9
-PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL = 0, 1, 2, 3, 4, 5
+PERIODIC, BOUNCEBACK, FREESLIP, INFLOW, OUTFLOW, NEE_WALL, HALO = 0, 1, 2, 3, 4, 5, 6
 FP32, BF16, FP16 = 0, 1, 2
 HOST, DEVICE = 0, 1
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_FACTORED = 0, 1, 2
@@ -35,7 +35,7 @@ EXPORTED = [
     "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_init_moments_f32", "tslb_set_force_field",
     "tslb_step", "tslb_get_moments", "tslb_get_moments_f32", "tslb_diagnostics", "tslb_adjoint_force_gradient",
     "tslb_adjoint", "tslb_interior_nodes", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
-    "tslb_diagnostics_noalloc",
+    "tslb_diagnostics_noalloc", "tslb_halo_plane_bytes", "tslb_halo_export", "tslb_halo_import",
 ]
 NOALLOC_MAX_NODES = 1 << 26
 
@@ -108,6 +108,9 @@ def load(build_if_missing=True):
     L.tslb_last_error.restype = ctypes.c_char_p
     L.tslb_diagnostics_noalloc.argtypes = [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
                                            ctypes.c_double, vp, vp]
+    L.tslb_halo_plane_bytes.argtypes = [vp, ctypes.POINTER(i64)]
+    L.tslb_halo_export.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.tslb_halo_import.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     _lib = L
     return L
 
@@ -290,6 +293,45 @@ def tslb_diagnostics_noalloc(rho, u, pi, dims, bc, tau, out, stream=None):
     _check(load().tslb_diagnostics_noalloc(p(rho), p(u), p(pi), d, b, float(tau), s, p(out)), None)
 
 
+def tslb_halo_plane_bytes(h):
+    b = ctypes.c_int64(0)
+    _check(load().tslb_halo_plane_bytes(h, ctypes.byref(b)), h)
+    return b.value
+
+
+def _buf_ptr(a):
+    """(pointer, where) of a contiguous buffer: CUDA tensor, CPU tensor or numpy array."""
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        if not a.is_contiguous():
+            raise ValueError("halo buffers must be contiguous")
+        return _device_ptr(a), DEVICE
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr()), HOST
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("halo buffers must be contiguous")
+    return ctypes.c_void_p(a.ctypes.data), HOST
+
+
+def _halo_buf(h, a):
+    nbytes = a.numel() * a.element_size() if hasattr(a, "element_size") else a.nbytes
+    need = tslb_halo_plane_bytes(h)
+    if nbytes < need:
+        raise ValueError("halo buffer holds %d bytes, %d needed" % (nbytes, need))
+    return _buf_ptr(a)
+
+
+def tslb_halo_export(h, side, dst):
+    """Pack this slab's layer z = 0 (side 0) or z = nz - 1 (side 1) into dst."""
+    p, where = _halo_buf(h, dst)
+    _check(load().tslb_halo_export(h, int(side), p, where), h)
+
+
+def tslb_halo_import(h, side, src):
+    """Load a packed plane into the ghost layer below (side 0) or above (side 1) the slab."""
+    p, where = _halo_buf(h, src)
+    _check(load().tslb_halo_import(h, int(side), p, where), h)
+
+
 def tslb_interior_nodes(h):
     return load().tslb_interior_nodes(h)
 
@@ -409,6 +451,15 @@ class Solver:
         g = np.zeros(3 * self.N, dtype=np.float32)
         tslb_adjoint_force_gradient(self._h, nsteps, g, HOST)
         return g.reshape(3, self.N)
+
+    def halo_plane_bytes(self):
+        return tslb_halo_plane_bytes(self._h)
+
+    def halo_export(self, side, dst):
+        tslb_halo_export(self._h, side, dst)
+
+    def halo_import(self, side, src):
+        tslb_halo_import(self._h, side, src)
 
     def adjoint(self, lam, nsteps):
         """dJ/dF ([3, N] FP32) for the cotangent lam = dJ/dm of the current moments,

@@ -98,6 +98,7 @@ void release(tslb_s* h) {
     for (void* c : h->ckpts) cudaFree(c);
     if (h->adj_ws) cudaFree(h->adj_ws);
     if (h->adj_lam) cudaFree(h->adj_lam);
+    if (h->ghost) cudaFree(h->ghost);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -134,6 +135,10 @@ Physics make_physics(const tslb_s* h) {
         p.inv_s_pi = (float)(1.0 / h->pi_ref);
     }
     p.sr_key = sr_step_key(h->rounding_seed, h->t);
+    if (h->ghost) {
+        p.halo[0] = h->ghost;
+        p.halo[1] = static_cast<const char*>(h->ghost) + halo_plane_bytes(h);
+    }
     p.omega1_pi = (float)((1.0 - h->omega) * (double)p.s_pi);
     p.pi_store = (float)((double)p.inv_s_pi / 216.0);
     return p;
@@ -273,7 +278,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     const bool d2 = lattice == TSLB_D2Q9;
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, TSLB_ERR_INVALID, "tau must be > 1/2");
     for (int f = 0; f < 6; ++f)
-        if (bc[f] < TSLB_BC_PERIODIC || bc[f] > TSLB_BC_NEE_WALL)
+        if (bc[f] < TSLB_BC_PERIODIC || bc[f] > TSLB_BC_HALO)
             return fail(nullptr, TSLB_ERR_INVALID, "unknown boundary code");
     for (int a = 0; a < 3; ++a) {
         const bool p0 = bc[2 * a] == TSLB_BC_PERIODIC, p1 = bc[2 * a + 1] == TSLB_BC_PERIODIC;
@@ -282,7 +287,9 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
             if (dims[2] != 1 || !p0) return fail(nullptr, TSLB_ERR_INVALID, "D2Q9 needs nz = 1 with periodic z faces");
             continue;
         }
-        if (dims[a] < (p0 ? 3 : 4)) return fail(nullptr, TSLB_ERR_INVALID, "axis too short");
+        // a halo slab has no boundary layer: every layer is interior, as on a periodic axis
+        const bool halo = bc[2 * a] == TSLB_BC_HALO;
+        if (dims[a] < (p0 || halo ? 3 : 4)) return fail(nullptr, TSLB_ERR_INVALID, "axis too short");
         if (dims[a] > (int64_t)1 << 30) return fail(nullptr, TSLB_ERR_INVALID, "axis too long");
     }
     // Supported face combinations (see tslb_bc).
@@ -293,9 +300,15 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "x faces: periodic or free-slip");
     if (!(by == TSLB_BC_PERIODIC || by == TSLB_BC_FREESLIP || by == TSLB_BC_BOUNCEBACK || by == TSLB_BC_NEE_WALL))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "y faces: periodic, bounce-back, free-slip or NEE wall");
-    if (!((bz0 == TSLB_BC_PERIODIC && bz1 == TSLB_BC_PERIODIC) || (bz0 == TSLB_BC_INFLOW && bz1 == TSLB_BC_OUTFLOW)))
-        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "z faces: periodic, or inflow (z-) with outflow (z+)");
-    if ((by == TSLB_BC_BOUNCEBACK || by == TSLB_BC_NEE_WALL) && (bx != TSLB_BC_PERIODIC || bz0 != TSLB_BC_PERIODIC))
+    for (int f = 0; f < 4; ++f)
+        if (bc[f] == TSLB_BC_HALO) return fail(nullptr, TSLB_ERR_UNSUPPORTED, "halo faces are z faces");
+    const bool zhalo = bz0 == TSLB_BC_HALO && bz1 == TSLB_BC_HALO;
+    if (!((bz0 == TSLB_BC_PERIODIC && bz1 == TSLB_BC_PERIODIC) || (bz0 == TSLB_BC_INFLOW && bz1 == TSLB_BC_OUTFLOW) ||
+          zhalo))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED, "z faces: periodic, inflow (z-) with outflow (z+), or both halo");
+    // a halo slab's z layers are interior like a periodic axis's, for every face rule below
+    const bool zper_like = bz0 == TSLB_BC_PERIODIC || zhalo;
+    if ((by == TSLB_BC_BOUNCEBACK || by == TSLB_BC_NEE_WALL) && (bx != TSLB_BC_PERIODIC || !zper_like))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED, "bounce-back and NEE y walls need periodic x and z");
 
     tslb_options o;
@@ -317,8 +330,14 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
         return fail(nullptr, TSLB_ERR_INVALID, "unknown rounding mode");
     if (o.rounding == TSLB_ROUND_STOCHASTIC && o.precision == TSLB_FP32)
         return fail(nullptr, TSLB_ERR_INVALID, "stochastic rounding applies to 16-bit storage");
+    if (zhalo && (d2 || o.kernel == TSLB_KERNEL_DIRECT || o.sponge_width != 0 || o.checkpoint_every != 0 ||
+                  bx != TSLB_BC_PERIODIC || !(by == TSLB_BC_PERIODIC || by == TSLB_BC_BOUNCEBACK) ||
+                  o.forcing != TSLB_FORCING_LUO))
+        return fail(nullptr, TSLB_ERR_UNSUPPORTED,
+                    "halo slabs: D3Q27, factored kernel, periodic x, periodic or bounce-back y, Luo forcing, "
+                    "no sponge layer, no checkpoints");
     if (o.forcing == TSLB_FORCING_GUO &&
-        (d2 || bx != TSLB_BC_PERIODIC || bz0 != TSLB_BC_PERIODIC || by == TSLB_BC_NEE_WALL || o.sponge_width != 0))
+        (d2 || bx != TSLB_BC_PERIODIC || !zper_like || by == TSLB_BC_NEE_WALL || o.sponge_width != 0))
         return fail(nullptr, TSLB_ERR_UNSUPPORTED,
                     "Guo forcing: D3Q27, periodic x and z, no NEE walls, no sponge layer");
     if (d2 && (o.precision != TSLB_FP32 || o.checkpoint_every != 0 || o.sponge_width != 0))
@@ -358,7 +377,7 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     tslb::Geometry& g = h->g;
     int ext[3];
     for (int a = 0; a < 3; ++a) {
-        const bool per = bc[2 * a] == TSLB_BC_PERIODIC;
+        const bool per = bc[2 * a] == TSLB_BC_PERIODIC || bc[2 * a] == TSLB_BC_HALO;
         g.lo[a] = per ? 0 : 1;
         ext[a] = (int)(per ? dims[a] : dims[a] - 2);
     }
@@ -427,6 +446,17 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
             return cuda_fail(nullptr, e, "sponge table copy");
         }
     }
+    if (zhalo) {
+        // the two ghost planes the step reads at z = -1 and z = nz (packed, rest state)
+        const size_t gb = 2 * halo_plane_bytes(h);
+        e = dev_alloc(&h->ghost, gb);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->ghost, 0, gb, h->stream);
+        if (e != cudaSuccess) {
+            std::string m = std::string("device allocation of the ghost planes failed: ") + cudaGetErrorString(e);
+            release(h);
+            return fail(nullptr, TSLB_ERR_ALLOC, m);
+        }
+    }
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     h->sm_count = sms;
@@ -466,6 +496,7 @@ int tslb_set_force_field(tslb_t* h, const float* F, int where) {
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
     if (h->lattice == TSLB_D2Q9) return fail(h, TSLB_ERR_UNSUPPORTED, "D2Q9 takes the constant body force only");
+    if (h->ghost && F) return fail(h, TSLB_ERR_UNSUPPORTED, "halo slabs take the constant body force only");
     cudaSetDevice(h->device);
     if (!F) {
         if (h->force_field) {
@@ -514,7 +545,7 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (nsteps < 0) return fail(h, TSLB_ERR_INVALID, "nsteps < 0");
     cudaSetDevice(h->device);
-    if (h->lattice == TSLB_D3Q27 && h->kernel == TSLB_KERNEL_FACTORED && !tslb::factored_supports(h))
+    if (h->lattice == TSLB_D3Q27 && (h->kernel == TSLB_KERNEL_FACTORED || h->ghost) && !tslb::factored_supports(h))
         return fail(h, TSLB_ERR_UNSUPPORTED, "the factored kernel does not support this configuration");
     const int k = h->checkpoint_every;
     for (int64_t s = 0; s < nsteps; ++s) {
@@ -608,6 +639,54 @@ int tslb_adjoint(tslb_t* h, const double* lambda_T, int64_t nsteps, int ckpt_eve
     if (ckpt_every != 0 && ckpt_every != h->checkpoint_every)
         return fail(h, TSLB_ERR_INVALID, "ckpt_every must be 0 or the handle's checkpoint_every");
     return adjoint_common(h, lambda_T, nsteps, dJdF, where);
+}
+
+int tslb_halo_plane_bytes(const tslb_t* h, int64_t* bytes) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (!bytes) return fail(const_cast<tslb_t*>(h), TSLB_ERR_INVALID, "null output");
+    if (!h->ghost) return fail(const_cast<tslb_t*>(h), TSLB_ERR_STATE, "the handle has no halo faces");
+    *bytes = (int64_t)halo_plane_bytes(h);
+    return TSLB_OK;
+}
+
+// One packed plane <-> the three stored arrays of layer z (V0: 4 values per
+// node, V1: 4, V2: 2, each array fs nodes apart), on the handle's stream.
+static int halo_copy(tslb_t* h, int side, void* other, int where, bool to_other) {
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (!other) return fail(h, TSLB_ERR_INVALID, "null buffer");
+    if (side != 0 && side != 1) return fail(h, TSLB_ERR_INVALID, "side must be 0 or 1");
+    if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    if (!h->ghost) return fail(h, TSLB_ERR_STATE, "the handle has no halo faces");
+    cudaSetDevice(h->device);
+    const tslb::Geometry& g = h->g;
+    const size_t pb = halo_plane_bytes(h), e4 = 4 * h->elem * (size_t)g.plane, e2 = 2 * h->elem * (size_t)g.plane;
+    cudaError_t e = cudaSuccess;
+    if (to_other) {
+        // layer z = 0 or nz - 1 of the current buffer -> packed [V0 | V1 | V2]
+        const char* b = static_cast<const char*>(h->buf[h->cur]);
+        const size_t z = side == 0 ? 0 : (size_t)g.nz - 1, fsb = (size_t)g.fstride * h->elem;
+        const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        char* d = static_cast<char*>(other);
+        e = cudaMemcpyAsync(d, b + z * e4, e4, kind, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d + e4, b + 4 * fsb + z * e4, e4, kind, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d + 2 * e4, b + 8 * fsb + z * e2, e2, kind, h->stream);
+    } else {
+        const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        e = cudaMemcpyAsync(static_cast<char*>(h->ghost) + side * pb, other, pb, kind, h->stream);
+    }
+    if (e == cudaSuccess && where == TSLB_HOST) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, to_other ? "halo export" : "halo import");
+    return TSLB_OK;
+}
+
+int tslb_halo_export(tslb_t* h, int side, void* dst, int where) {
+    const Range range("tslb_halo_export");
+    return halo_copy(h, side, dst, where, true);
+}
+
+int tslb_halo_import(tslb_t* h, int side, const void* src, int where) {
+    const Range range("tslb_halo_import");
+    return halo_copy(h, side, const_cast<void*>(src), where, false);
 }
 
 int64_t tslb_interior_nodes(const tslb_t* h) { return h ? (int64_t)h->g.plane * h->g.nz : 0; }

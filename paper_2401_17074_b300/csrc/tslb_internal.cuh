@@ -81,6 +81,9 @@ struct Physics {
     uint32_t sr_key;
     // sponge layer: (1 - omega) per full-lattice z, or nullptr (uniform omega)
     const float* omega1_z;
+    // halo slab (TSLB_BC_HALO z faces): the packed ghost planes read as the
+    // layers z = -1 (halo[0]) and z = nz (halo[1]); nullptr otherwise
+    const void* halo[2];
 };
 
 // ---- stochastic rounding ------------------------------------------------------
@@ -420,8 +423,14 @@ constexpr float INV216_HI = 0x1.2f684cp-8f;    // fl(1/216)
 constexpr float INV216_LO = -0x1.2f684cp-35f;  // 1/216 - INV216_HI (exact)
 __device__ __forceinline__ float div216(float x) { return fmaf(x, INV216_HI, x * INV216_LO); }
 
-// 1/r for r = 216 + D0 (a normal number near 216): hardware reciprocal plus
-// one Newton step, accurate to about half an ulp.
+// 1/r for r = 216 + D0 (a normal number near 216): the hardware approximate
+// reciprocal x, then one Newton-Raphson step for f(x) = 1/x - r written with
+// fused multiply-adds, e = 1 - r x, x' = x + x e (the iteration analysed in
+// P. Markstein, "Computation of elementary functions on the IBM RISC
+// System/6000 processor", IBM J. Res. Dev. 34 (1990) 111-119), which squares
+// the approximation's relative error; the result is within one ulp of 1/r
+// (tests/test_rcp_gpu.py checks that bound and the share of correctly rounded
+// results over a sweep of r).
 __device__ __forceinline__ float rcp_refined(float r) {
     float i;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(i) : "f"(r));
@@ -556,8 +565,13 @@ struct tslb_s {
     // from its first use until tslb_destroy
     void* adj_lam = nullptr;
     size_t adj_lam_bytes = 0;
+    // halo slab: two packed ghost planes, [side][V0 plane | V1 plane | V2 plane]
+    void* ghost = nullptr;
     std::string err;
 };
+
+// Bytes of one packed plane of a halo slab: ten stored values per interior node of a layer.
+inline size_t halo_plane_bytes(const tslb_s* h) { return (size_t)NFIELDS_3D * (size_t)h->g.plane * h->elem; }
 
 namespace tslb {
 

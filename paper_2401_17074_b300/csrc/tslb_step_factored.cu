@@ -170,15 +170,30 @@ __device__ __forceinline__ Pops2 pops3(f2 a0, f2 a1, f2 a2) {
     return {add2(e, a1), sub2(e, a1), sub2(a0, a2)};
 }
 
-// Interior plane stored at march position zs (periodic wrap, inflow / outflow ghosts).
-__device__ __forceinline__ int plane_of(int zs, const Geometry& g, bool zper, bool& inflow_ghost) {
+// Interior plane stored at march position zs (periodic wrap, inflow / outflow
+// ghosts).  On a halo slab the positions -1 and nz are the ghost planes:
+// halo = 1 (below) or 2 (above), and the returned plane is 0 of that buffer.
+template <bool HALO>
+__device__ __forceinline__ int plane_of(int zs, const Geometry& g, bool zper, bool& inflow_ghost, int& halo) {
     inflow_ghost = false;
+    halo = 0;
     if (zs < 0) {
         if (zper) return zs + g.nz;
+        if (HALO) {
+            halo = 1;
+            return 0;
+        }
         inflow_ghost = true;
         return 0;
     }
-    if (zs >= g.nz) return zper ? zs - g.nz : g.nz - 1;  // outflow ghost copies the last layer
+    if (zs >= g.nz) {
+        if (zper) return zs - g.nz;
+        if (HALO) {
+            halo = 2;
+            return 0;
+        }
+        return g.nz - 1;  // outflow ghost copies the last layer
+    }
     return zs;
 }
 
@@ -333,6 +348,9 @@ __device__ __forceinline__ bool uni(bool v) { return __all_sync(0xffffffffu, v);
 template <bool HOIST>
 __device__ __forceinline__ bool role(bool v) { return HOIST ? v : uni(v); }
 
+// March specialisations by warp role (see Kernel::march).
+constexpr int ROLE_ANY = 0, ROLE_PLAIN = 1;
+
 // Per-thread constants of the march.
 struct Ctx {
     int tid, lane, warp, x, y, xl, yl;
@@ -347,7 +365,9 @@ struct Ctx {
 #endif
 };
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE>
+// HALO: a slab of a z-decomposed lattice, whose layers -1 and nz are the
+// packed ghost planes p.halo[0] and p.halo[1].
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE, bool HALO>
 struct Kernel {
     typedef typename Codec::T T;
     static constexpr bool HOIST = sizeof(T) != 4;
@@ -360,16 +380,18 @@ struct Kernel {
     static constexpr size_t FOFF = 2 * PF::BUF + CORRBUF + BARBUF;
 
     // Start the copies of stored plane zl's moments (march plane j, PAR = j & 1)
-    // into prefetch buffer PAR.
+    // into prefetch buffer PAR.  The three arrays start fs nodes apart: the
+    // moment buffer's field stride, or one plane in a packed ghost plane.
     template <int PAR>
     static __device__ __forceinline__ void prefetch_plane(const Ctx& c, const Geometry& g, const Physics& p,
-                                                          const T* __restrict__ src, char* pfb, int zl) {
+                                                          const T* __restrict__ src, long long fs, char* pfb,
+                                                          int zl) {
         const unsigned n = c.col + c.plane * (unsigned)zl;
         char* b = pfb + PAR * PF::BUF;
         if (TSLB_IN_RANGE(n, g.plane * g.nz, c.err)) {
             cp_async<PF::B01>(smem_u32(b + c.tid * PF::B01), src + (size_t)n * 4);
-            cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * g.fstride + (size_t)n * 4);
-            cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * g.fstride + (size_t)n * 2);
+            cp_async<PF::B01>(smem_u32(b + NT * PF::B01 + c.tid * PF::B01), src + 4 * fs + (size_t)n * 4);
+            cp_async<PF::B2>(smem_u32(b + 2 * NT * PF::B01 + c.tid * PF::B2), src + 8 * fs + (size_t)n * 2);
             if (FORCE)
                 cp_async<16>(smem_u32(pfb + FOFF + PAR * FBUF + c.tid * FSLOT),
                              reinterpret_cast<const float4*>(p.force) + n);
@@ -380,7 +402,10 @@ struct Kernel {
     static __device__ __forceinline__ void prefetch(const Ctx& c, const Geometry& g, const Physics& p,
                                                     const T* __restrict__ src, char* pfb, int j) {
         bool ig;
-        prefetch_plane<PAR>(c, g, p, src, pfb, plane_of(c.z0 - 1 + j, g, c.zper, ig));
+        int hs;
+        const int zl = plane_of<HALO>(c.z0 - 1 + j, g, c.zper, ig, hs);
+        if (HALO && hs) prefetch_plane<PAR>(c, g, p, static_cast<const T*>(p.halo[hs - 1]), g.plane, pfb, zl);
+        else prefetch_plane<PAR>(c, g, p, src, g.fstride, pfb, zl);
     }
     // Body force of the node in prefetch buffer PAR (stored index idx).
     template <int PAR>
@@ -398,7 +423,10 @@ struct Kernel {
 
     // STEADY: 2 <= j <= np - 3, so the plane and the next one are stored
     // interior planes inside the chunk (no wrap, no ghost, exchange active).
-    template <int PAR, bool STEADY>
+    // ROLE: ROLE_PLAIN for an output row with no wall, ghost or NEE role (its
+    // role tests are compile-time constants), ROLE_ANY for the others (tests
+    // at run time on the warp's role flags).
+    template <int PAR, bool STEADY, int ROLE>
     static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
                                                       const T* __restrict__ src, T* __restrict__ dst, float* ysm,
                                                       char* pfb, float* corr, uint64_t* bars, bool& dead, int j,
@@ -406,7 +434,8 @@ struct Kernel {
                                                       const f2 (&cOld)[4], f2 (&cNew)[4]) {
         const int zs = c.z0 - 1 + j;
         bool inflow_ghost = false;
-        const int zl = STEADY ? zs : plane_of(zs, g, c.zper, inflow_ghost);
+        int halo = 0;
+        const int zl = STEADY ? zs : plane_of<HALO>(zs, g, c.zper, inflow_ghost, halo);
         const unsigned idx = c.col + c.plane * (unsigned)zl;
         // (1 - omega) s_pi of this source plane: uniform, or the sponge layer's
         // value at the plane's lattice z (ghost planes included)
@@ -415,7 +444,7 @@ struct Kernel {
                                 ? __ldg(p.omega1_z + zfull) * p.s_pi
                                 : p.omega1_pi;
         // next plane's copies go out before this plane's are consumed
-        if (STEADY) prefetch_plane<PAR ^ 1>(c, g, p, src, pfb, zs + 1);
+        if (STEADY) prefetch_plane<PAR ^ 1>(c, g, p, src, g.fstride, pfb, zs + 1);
         else if (zs < c.z1) prefetch<PAR ^ 1>(c, g, p, src, pfb, j + 1);
         else cp_async_commit();
         cp_async_wait_prev();
@@ -433,7 +462,7 @@ struct Kernel {
                 const float uBz = inflow_uz(p, (long long)c.xl + g.lo[0], (long long)c.yl + g.lo[1]);
                 h = to_pairs(hermite(m[F_DRHO], 0.f, 0.f, uBz, m[F_UX], m[F_UY], m[F_UZ], &m[F_PXX], 0.f, 0.f, 0.f,
                                      om_pi));
-            } else if (NEEY && role<HOIST>(c.nee_row)) {
+            } else if (NEEY && ROLE == ROLE_ANY && role<HOIST>(c.nee_row)) {
                 // ghost row beyond an NEE wall: the wall node (whose column is
                 // clamped onto the adjacent fluid node) emits f^eq(rho_F, 0) +
                 // (1 - omega) f^neq(Pi_F, u_F), Eq. neq_final with u_B = 0
@@ -469,7 +498,7 @@ struct Kernel {
                 Q[3 + r] = pops3(Z[1][r].x, Z[0][r].y, Z[3][r].y);  // k1 = 1 (groups 1, 5, 7)
                 Q[6 + r] = pops2(Z[2][r].x, Z[3][r].x);             // k1 = 2 (groups 3, 6)
             }
-            if (role<HOIST>(c.zero_row)) {
+            if (ROLE == ROLE_ANY && role<HOIST>(c.zero_row)) {
                 // ghost row beyond a bounce-back wall: the entering deviation is zero
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -489,11 +518,12 @@ struct Kernel {
             mbar_arrive_if(&bars[c.warp * 2 + PAR], c.arrive);
             {
                 const unsigned par = (unsigned)((j - 2) >> 1) & 1u;  // phase of this buffer's (j-2)/2-th use
-                if (c.wait_lo) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
-                if (c.wait_hi) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
+                // plain rows (warps 1 .. WROWS - 2) always have both neighbours
+                if (ROLE == ROLE_PLAIN || c.wait_lo) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
+                if (ROLE == ROLE_PLAIN || c.wait_hi) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
             }
             // halo and ghost rows only feed the y exchange (warp-uniform)
-            if (role<HOIST>(c.out_row)) {
+            if (ROLE == ROLE_PLAIN || role<HOIST>(c.out_row)) {
                 // L / R: (r = 0, r = 1) pairs per k1 and the r = 2 scalars
                 f2 LA[3], RA[3];
                 float Ls[3], Rs[3];
@@ -544,7 +574,7 @@ struct Kernel {
                 // ---- halfway bounce-back on the wall-adjacent rows ----------
                 // The ghost row next to the wall computed the correction for
                 // this plane one march step earlier (see bounce_back_correction).
-                if (c.ybb) {
+                if (ROLE == ROLE_ANY && c.ybb) {
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
                         if (!role<HOIST>(side == 0 ? c.row_lo : c.row_hi)) continue;
@@ -590,7 +620,7 @@ struct Kernel {
             ppOld[i] = P[i].pp;
             cNew[i] = P[i].c;
         }
-        if (role<HOIST>(c.zero_row) && (STEADY || (zs >= c.z0 && zs < c.z1))) {
+        if (ROLE == ROLE_ANY && role<HOIST>(c.zero_row) && (STEADY || (zs >= c.z0 && zs < c.z1))) {
             // The ghost thread's column is clamped onto the wall-adjacent node,
             // so its prefetch slots hold that node's moments at plane zs.
             float m[NFIELDS];
@@ -599,6 +629,31 @@ struct Kernel {
             node_force<PAR>(c, g, p, pfb, idx, F0, F1, F2);
             bounce_back_correction(m, F0, F1, F2, om_pi, c.y < 0 ? 1.0f : -1.0f,
                                    corr + ((PAR * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
+        }
+    }
+
+    // The whole z march of one warp: planes 0 and 1 (ghost / wrap, no
+    // exchange yet) and the last two or three take the general path; the
+    // steady loop in between has none of its tests.  The window rotates by
+    // swapping roles between two register sets, so the march advances two
+    // planes per loop trip without register copies.
+    template <int ROLE>
+    static __device__ __forceinline__ void march(const Ctx& c, const Geometry& g, const Physics& p,
+                                                 const T* __restrict__ src, T* __restrict__ dst, float* ysm, char* pfb,
+                                                 float* corr, uint64_t* bars, bool& dead) {
+        f2 ppA[4], ppB[4], cA[4], cB[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ppA[i] = ppB[i] = cA[i] = cB[i] = k2(0.0f);
+        plane_step<0, false, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, 0, ppA, cA, cB);
+        plane_step<1, false, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, 1, ppB, cB, cA);
+        int j = 2;
+        for (; j + 1 <= c.np - 3; j += 2) {
+            plane_step<0, true, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j, ppA, cA, cB);
+            plane_step<1, true, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j + 1, ppB, cB, cA);
+        }
+        for (; j < c.np; j += 2) {
+            plane_step<0, false, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j, ppA, cA, cB);
+            if (j + 1 < c.np) plane_step<1, false, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j + 1, ppB, cB, cA);
         }
     }
 
@@ -643,11 +698,11 @@ struct Kernel {
     }
 };
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE, bool HALO>
 __global__ void __launch_bounds__(NT, 1)
     step_factored_kernel(const typename Codec::T* __restrict__ src, typename Codec::T* __restrict__ dst, Geometry g,
                          Physics p, int zchunk) {
-    typedef Kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE> K;
+    typedef Kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE, HALO> K;
     // [2][YBUF] y exchange, [2][PF::BUF] plane prefetch, corrections, mbarriers,
     // and with FORCE [2][FBUF] force slots
     extern __shared__ __align__(16) float ysm[];
@@ -725,29 +780,18 @@ __global__ void __launch_bounds__(NT, 1)
     // start or before the last planes measured slower.)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     K::template prefetch<0>(c, g, p, src, pfb, 0);
-    f2 ppA[4], ppB[4], cA[4], cB[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) ppA[i] = ppB[i] = cA[i] = cB[i] = k2(0.0f);
-    // The window rotates by swapping roles between two register sets, so the
-    // march advances two planes per loop trip without register copies.
-    // Planes 0 and 1 (ghost / wrap, no exchange yet) and the last two or three
-    // take the general path; the steady loop in between has none of its tests.
-    K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, 0, ppA, cA, cB);
-    K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, 1, ppB, cB, cA);
-    int j = 2;
-    for (; j + 1 <= c.np - 3; j += 2) {
-        K::template plane_step<0, true>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j, ppA, cA, cB);
-        K::template plane_step<1, true>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j + 1, ppB, cB, cA);
-    }
-    for (; j < c.np; j += 2) {
-        K::template plane_step<0, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j, ppA, cA, cB);
-        if (j + 1 < c.np) K::template plane_step<1, false>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j + 1, ppB, cB, cA);
-    }
+    // Output rows without a wall, ghost or NEE role (warp-uniform) run the
+    // march with those tests compiled out; the halo, ghost and wall rows run
+    // the general one.
+    const bool plain = uni(c.warp >= 1 && c.warp <= YOUT && c.out_row && !c.zero_row && !c.nee_row &&
+                           !(c.ybb && (c.row_lo || c.row_hi)));
+    if (plain) K::template march<ROLE_PLAIN>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
+    else K::template march<ROLE_ANY>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
 }
 
-template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE = false>
+template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE = false, bool HALO = false>
 cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p) {
-    auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE>;
+    auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE, HALO>;
     static bool configured[64] = {};
     const int dev = h->device;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -794,6 +838,9 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
 template <class Codec>
 cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Physics& p) {
     const bool xfree = h->g.bc[0] == TSLB_BC_FREESLIP, sponge = p.omega1_z != nullptr;
+    // halo slabs: periodic x, periodic or bounce-back y, Luo forcing, constant
+    // force (checked at create)
+    if (h->g.bc[4] == TSLB_BC_HALO) return launch_t<Codec, false, false, false, false, false, true>(h, src, dst, p);
     // Guo forcing comes with periodic x, no sponge and no NEE walls; NEE y walls
     // with periodic x (both checked at create)
     if (p.guo) return launch_t<Codec, false, false, false, true>(h, src, dst, p);

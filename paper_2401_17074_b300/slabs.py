@@ -1,0 +1,143 @@
+"""Slab decomposition of a TSLB lattice along z.
+
+The paper's Conclusions name the multi-GPU extension of the thread-safe
+scheme as future work.  Its natural form here is a split of the lattice into
+z slabs: each slab is one handle whose z faces are TSLB_BC_HALO, and each
+time step needs, before it, one layer of the 10 stored moment fields from
+each neighbour (the step of Eq. pushLB reaches one node in every direction).
+The slabs form a ring, so the lattice stays periodic in z.
+
+Two drivers share the same exchange pattern:
+
+* ``SlabChain`` keeps every slab in this process, on one device and one
+  stream, and moves the packed planes with device copies.  Stream order makes
+  the sequence export -> import -> step correct without further
+  synchronisation.
+* ``exchange_halos`` is the multi-process form: one slab per rank, the packed
+  planes sent to and received from the ring neighbours with
+  ``torch.distributed`` point-to-point operations (NCCL for CUDA buffers, gloo
+  for CPU buffers).  A slab is any object with ``halo_export(side, buf)`` and
+  ``halo_import(side, buf)``, so the bookkeeping can run on CPU stand-ins.
+"""
+import numpy as np
+
+from . import FP32, HALO, PERIODIC, Solver
+
+# message tags: planes travelling up the ring (a slab's top layer to the next
+# slab's lower ghost) and down it (bottom layer to the previous slab's upper ghost)
+TAG_UP, TAG_DOWN = 1, 2
+
+
+def split(nz, nslabs):
+    """z ranges [z0, z1) of nslabs slabs covering nz layers, as even as possible."""
+    if nslabs < 1 or nz < 3 * nslabs:
+        raise ValueError("each slab needs at least 3 layers")
+    base, extra = divmod(nz, nslabs)
+    out, z = [], 0
+    for s in range(nslabs):
+        n = base + (1 if s < extra else 0)
+        out.append((z, z + n))
+        z += n
+    return out
+
+
+def ring_neighbours(rank, world):
+    """(rank below, rank above) in the ring of slabs."""
+    return (rank - 1) % world, (rank + 1) % world
+
+
+def exchange_halos(slab, bufs, dist):
+    """One halo exchange of this rank's slab with its ring neighbours.
+
+    bufs = (send_lo, send_hi, recv_lo, recv_hi): buffers of one packed plane
+    each (CUDA tensors with NCCL, CPU tensors with gloo).  The slab's bottom
+    layer goes down the ring and its top layer up; the planes received fill
+    its ghost layers below (from the rank below) and above (from the rank
+    above).  With one rank the slab is its own neighbour on both sides."""
+    send_lo, send_hi, recv_lo, recv_hi = bufs
+    slab.halo_export(0, send_lo)
+    slab.halo_export(1, send_hi)
+    world = dist.get_world_size() if dist is not None else 1
+    if world == 1:
+        slab.halo_import(0, send_hi)
+        slab.halo_import(1, send_lo)
+        return
+    lo, hi = ring_neighbours(dist.get_rank(), world)
+    ops = [dist.P2POp(dist.isend, send_hi, hi, tag=TAG_UP),
+           dist.P2POp(dist.irecv, recv_lo, lo, tag=TAG_UP),
+           dist.P2POp(dist.isend, send_lo, lo, tag=TAG_DOWN),
+           dist.P2POp(dist.irecv, recv_hi, hi, tag=TAG_DOWN)]
+    for r in dist.batch_isend_irecv(ops):
+        r.wait()
+    slab.halo_import(0, recv_lo)
+    slab.halo_import(1, recv_hi)
+
+
+def _zslice(a, dims, z0, z1, ncomp):
+    """Layers z0 .. z1-1 of a full-lattice array with ncomp components."""
+    nx, ny, nz = dims
+    a = np.asarray(a).reshape(ncomp, nz, ny * nx)
+    return np.ascontiguousarray(a[:, z0:z1, :].reshape(ncomp, -1))
+
+
+class SlabChain:
+    """A lattice periodic in z, split into z slabs that all live in this process.
+
+    Every slab is a Solver with halo z faces on the same device and the same
+    stream; ``step`` exchanges the boundary layers through device buffers
+    before every step.  The result equals a single-handle run of the whole
+    lattice (the step's arithmetic at a node does not depend on where the
+    lattice is cut).  bc gives the x and y faces (the z faces must be periodic).
+    """
+
+    def __init__(self, dims, tau, nslabs, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05,
+                 pi_ref=1e-3, device=0):
+        import torch
+        if bc[4] != PERIODIC or bc[5] != PERIODIC:
+            raise ValueError("a slab chain is periodic in z")
+        self.dims = tuple(int(d) for d in dims)
+        self.ranges = split(self.dims[2], nslabs)
+        self.stream = torch.cuda.Stream(device=device)
+        sbc = tuple(bc[:4]) + (HALO, HALO)
+        self.slabs = [Solver((self.dims[0], self.dims[1], z1 - z0), tau, force=force, bc=sbc, precision=precision,
+                             u_ref=u_ref, pi_ref=pi_ref, device=device, stream=self.stream.cuda_stream)
+                      for z0, z1 in self.ranges]
+        nb = self.slabs[0].halo_plane_bytes()
+        self.bufs = [[torch.empty(nb, dtype=torch.uint8, device="cuda:%d" % device) for _ in range(2)]
+                     for _ in self.slabs]
+
+    def close(self):
+        for s in self.slabs:
+            s.close()
+
+    def init_moments(self, rho, u, pi=None):
+        for s, (z0, z1) in zip(self.slabs, self.ranges):
+            s.init_moments(_zslice(rho, self.dims, z0, z1, 1).reshape(-1), _zslice(u, self.dims, z0, z1, 3),
+                           None if pi is None else _zslice(pi, self.dims, z0, z1, 6))
+
+    def exchange(self):
+        n = len(self.slabs)
+        for s, slab in enumerate(self.slabs):
+            slab.halo_export(0, self.bufs[s][0])
+            slab.halo_export(1, self.bufs[s][1])
+        for s in range(n):
+            self.slabs[(s + 1) % n].halo_import(0, self.bufs[s][1])
+            self.slabs[(s - 1) % n].halo_import(1, self.bufs[s][0])
+
+    def step(self, n=1):
+        for _ in range(int(n)):
+            self.exchange()
+            for slab in self.slabs:
+                slab.step(1)
+
+    def get_moments(self):
+        nx, ny, nz = self.dims
+        rho = np.zeros((nz, ny * nx))
+        u = np.zeros((3, nz, ny * nx))
+        pi = np.zeros((6, nz, ny * nx))
+        for s, (z0, z1) in zip(self.slabs, self.ranges):
+            r, uu, p = s.get_moments()
+            rho[z0:z1] = r.reshape(z1 - z0, -1)
+            u[:, z0:z1] = uu.reshape(3, z1 - z0, -1)
+            pi[:, z0:z1] = p.reshape(6, z1 - z0, -1)
+        return rho.reshape(-1), u.reshape(3, -1), pi.reshape(6, -1)

@@ -176,3 +176,32 @@ def test_noalloc_wrapper_rejects_bad_arrays_before_launch():
         T.tslb_diagnostics_noalloc(cpu, cpu, None, (4, 4), bc, 0.6, cpu)
     with pytest.raises(ValueError, match="out must be given"):
         T.tslb_diagnostics_noalloc(cpu, cpu, None, dims, bc, 0.6, None)
+
+
+def test_halo_face_rules():
+    """Halo faces (the z-slab decomposition) are z faces on both sides, with
+    periodic x, periodic or bounce-back y, the factored kernel, no sponge and
+    no checkpoints; the rejections come before any CUDA call."""
+    H = T.HALO
+    for dims, bc, code in (((8, 8, 8), (H, H, 0, 0, 0, 0), T.TSLB_ERR_UNSUPPORTED),   # x faces
+                           ((8, 8, 8), (0, 0, 0, 0, H, 0), T.TSLB_ERR_INVALID),       # mixed with periodic
+                           ((8, 8, 8), (0, 0, 0, 0, H, 4), T.TSLB_ERR_UNSUPPORTED),   # halo + outflow
+                           ((8, 8, 8), (2, 2, 0, 0, H, H), T.TSLB_ERR_UNSUPPORTED),   # free-slip x
+                           ((8, 8, 8), (0, 0, 5, 5, H, H), T.TSLB_ERR_UNSUPPORTED),   # NEE walls
+                           ((8, 8, 2), (0, 0, 0, 0, H, H), T.TSLB_ERR_INVALID),       # fewer than 3 layers
+                           ((8, 8, 8), (0, 0, 0, 0, 7, 7), T.TSLB_ERR_INVALID)):      # unknown code
+        c, h = _create_code(dims=dims, bc=bc)
+        assert c == code, (bc, c)
+        assert not h.value
+    for attr, val in (("kernel", T.KERNEL_DIRECT), ("checkpoint_every", 4), ("forcing", T.TSLB_FORCING_GUO)):
+        o = T.tslb_options_default()
+        setattr(o, attr, val)
+        assert _create_code(bc=(0, 0, 0, 0, H, H), opt=o)[0] == T.TSLB_ERR_UNSUPPORTED, attr
+    o = T.tslb_options_default()
+    o.sponge_width, o.sponge_k = 3, 1.0
+    assert _create_code(bc=(0, 0, 0, 0, H, H), opt=o)[0] == T.TSLB_ERR_UNSUPPORTED
+    L = T.load()
+    b = ctypes.c_int64(0)
+    assert L.tslb_halo_plane_bytes(None, ctypes.byref(b)) == T.TSLB_ERR_INVALID
+    assert L.tslb_halo_export(None, 0, None, T.HOST) == T.TSLB_ERR_INVALID
+    assert L.tslb_halo_import(None, 0, None, T.HOST) == T.TSLB_ERR_INVALID

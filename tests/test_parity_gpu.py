@@ -3,10 +3,11 @@
 Both kernels (direct and sum-factorised) run through the C ABI on the same
 seeded inputs as the oracle.  The FP32 tolerance follows the target of the
 method's GPU form: 1e-5 relative L2 per field after 200 steps of the
-Taylor-Green vortex, 1e-6 after one step on random moments (only FP32
-rounding and summation order differ).  Relative errors are per field,
-||gpu - oracle||_2 / ||oracle||_2 over interior nodes, with rho compared as
-rho - 1.
+Taylor-Green vortex (rho - 1 excepted, see that test), 2e-6 after one step
+on random moments (only FP32 rounding and summation order differ).  Relative
+errors are per field, ||gpu - oracle||_2 / ||oracle||_2 over interior nodes,
+with rho compared as rho - 1.  Every comparison prints its measured per-field
+errors (pytest -s shows them).
 """
 import numpy as np
 import pytest
@@ -66,6 +67,8 @@ def run_pair(dims, tau, state, nsteps, kernel, bc=(0,) * 6, force=(0.0, 0.0, 0.0
 
 
 def assert_all_below(errs, tol, fields=FIELDS):
+    print("relative L2 error per field (bound %.1e on %s): %s"
+          % (tol, ",".join(fields), " ".join("%s %.2e" % (k, v) for k, v in errs.items())))
     bad = {k: v for k, v in errs.items() if k in fields and not v <= tol}
     assert not bad, "fields above %.1e: %s (all: %s)" % (tol, bad, errs)
 
@@ -89,10 +92,16 @@ def test_taylor_green_200_steps(cuda_ok, kernel):
     dims, state = W.taylor_green(n=32, u0=0.05, tau=0.6)
     errs, gpu, ref = run_pair(dims, 0.6, state, 200, kernel)
     assert_all_below(errs, 1e-5, fields=["ux", "uy", "pxx", "pyy"])
-    # rho - 1 is a small difference of divergence-cancelling mass fluxes; FP32
-    # storage and mode rounding of u put its floor near 1e-5 (an FP32 emulation
-    # of the same algorithm gives 0.9e-5, FP64 arithmetic with FP32 storage
-    # 0.2e-5).  It is held to 2e-5.
+    # rho - 1 is a small difference of divergence-cancelling mass fluxes, so
+    # its FP32 error relative to its own (small) norm sits near the 1e-5
+    # target: an FP32 emulation of the factored arithmetic over six TGVs with
+    # u0 perturbed in the last bits gives 0.79e-5 .. 1.32e-5 (rms 0.99e-5);
+    # FP64 arithmetic with FP32 storage gives 0.28e-5, and every arithmetic
+    # stage contributes about 0.3e-5 .. 0.7e-5 alone.  Separating the odd
+    # (momentum) parts of the 1-D populations in the density chain of the x
+    # and y passes leaves the ensemble unchanged (rms 0.94e-5), so no cheap
+    # compensation reaches 1e-5 with margin.  The measured value is printed
+    # and held to the 2e-5 bound.
     assert_all_below(errs, 2e-5, fields=["drho"])
     mask = interior_mask(dims, (0,) * 6)
     u_scale = np.abs(ref[1]).max()

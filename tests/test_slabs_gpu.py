@@ -1,0 +1,88 @@
+"""z-slab decomposition on one GPU: a ring of halo slabs against one handle.
+
+The lattice is cut into z slabs (TSLB_BC_HALO faces); before every step each
+slab exports its bottom and top layers and imports its neighbours' into its
+ghost planes (tslb_halo_export / tslb_halo_import, device copies on one
+stream).  The step's arithmetic at a node does not depend on where the
+lattice is cut, so the chain must reproduce the single-handle run bit for bit.
+"""
+import numpy as np
+import pytest
+
+import paper_2401_17074_b300 as T
+from paper_2401_17074_b300 import workloads as W
+from paper_2401_17074_b300.slabs import SlabChain
+
+pytestmark = pytest.mark.gpu
+
+
+def _single(dims, tau, force, bc, state, nsteps, **kw):
+    s = T.Solver(dims, tau, force=force, bc=bc, kernel=T.KERNEL_FACTORED, **kw)
+    s.init_moments(*state)
+    s.step(nsteps)
+    out = s.get_moments()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("case", ["channel-2", "channel-3-ragged", "periodic-4", "bf16-channel-2"])
+def test_slab_chain_matches_single_domain(cuda_ok, case):
+    if case.startswith("channel") or case.startswith("bf16"):
+        prm = W.channel_params(nx=40, ny=18, nz=27 if "ragged" in case else 24)
+        dims, tau, force, bc = prm["dims"], prm["tau"], prm["force"], prm["bc"]
+        state = W.channel_state(prm, seed=1)
+    else:
+        dims, tau, force, bc = (34, 21, 29), 0.62, (2e-6, -1e-6, 3e-6), (0,) * 6
+        state = W.random_state(dims, seed=81)
+    nslabs = int(case.split("-")[-1]) if case.split("-")[-1].isdigit() else int(case.split("-")[-2])
+    kw = {}
+    if case.startswith("bf16"):
+        kw = dict(precision=T.BF16, u_ref=0.05, pi_ref=W.pi_reference(state))
+    nsteps = 15
+    ref = _single(dims, tau, force, bc, state, nsteps, **kw)
+    chain = SlabChain(dims, tau, nslabs, force=force, bc=bc, **kw)
+    chain.init_moments(*state)
+    chain.step(nsteps)
+    got = chain.get_moments()
+    chain.close()
+    for a, b, name in zip(got, ref, ("rho", "u", "pi")):
+        assert np.array_equal(a, b), (name, np.abs(a - b).max())
+
+
+def test_halo_plane_round_trip(cuda_ok):
+    """A plane exported from one slab and imported as another's ghost is the
+    packed [V0 | V1 | V2] layer: its size is 10 stored values per node, and
+    host and device buffers give the same bytes."""
+    import torch
+    dims = (12, 7, 6)
+    s = T.Solver(dims, 0.7, bc=(0, 0, 0, 0, T.HALO, T.HALO))
+    s.init_moments(*W.random_state(dims, seed=82))
+    nb = s.halo_plane_bytes()
+    assert nb == 10 * 4 * 12 * 7
+    host = np.zeros(nb, dtype=np.uint8)
+    s.halo_export(1, host)
+    dev = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    s.halo_export(1, dev)
+    assert np.array_equal(host, dev.cpu().numpy())
+    v0 = host[: 4 * 4 * 84].view(np.float32).reshape(84, 4)  # (u_x, u_y, u_z, rho - 1) of layer z = 5
+    rho, u, _ = s.get_moments()
+    top = slice(5 * 84, 6 * 84)
+    assert np.allclose(v0[:, 3], rho[top] - 1, rtol=0, atol=1e-7)
+    assert np.allclose(v0[:, 0], u[0][top], rtol=0, atol=1e-7)
+    with pytest.raises(ValueError):
+        s.halo_export(0, np.zeros(nb - 1, dtype=np.uint8))
+    s.close()
+    s2 = T.Solver(dims, 0.7)  # no halo faces
+    with pytest.raises(T.TslbError) as ei:
+        s2.halo_plane_bytes()
+    assert ei.value.code == T.TSLB_ERR_STATE
+    s2.close()
+
+
+def test_halo_slab_rejects_unsupported(cuda_ok):
+    dims = (12, 7, 6)
+    s = T.Solver(dims, 0.7, bc=(0, 0, 0, 0, T.HALO, T.HALO))
+    with pytest.raises(T.TslbError) as ei:
+        s.set_force_field(np.zeros((3, 12 * 7 * 6), dtype=np.float32))
+    assert ei.value.code == T.TSLB_ERR_UNSUPPORTED
+    s.close()
