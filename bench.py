@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workload lines")
     ap.add_argument("--no-precision-study", action="store_true",
                     help="skip the time-averaged FP32 / BF16 / FP16 channel statistics")
-    ap.add_argument("--only", default=None, choices=["d2q9", "adjoint"],
+    ap.add_argument("--warm", type=int, default=200000, help="precision-study: FP32 steps before the branch")
+    ap.add_argument("--window", type=int, default=50000, help="precision-study: steps averaged per run")
+    ap.add_argument("--only", default=None, choices=["d2q9", "adjoint", "precision-study"],
                     help="time one extra workload alone (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -402,6 +404,89 @@ def precision_study(T, torch, stream, prm, state, warm=1000, window=5000, every=
     return out
 
 
+def turbulent_precision_study(T, torch, warm=200000, window=50000, every=1000, check=10000):
+    """Config 4 on developed turbulence: the full channel from a disturbed state
+    (workloads.channel_transition_state) run in FP32 for `warm` steps, its
+    bulk velocity, wall shear and maximum speed recorded every `check` steps;
+    then, from that state, runs of `window` steps in FP32, in FP32 from the
+    same state with a 1e-7 relative perturbation of u (the chaotic noise floor
+    of the statistics), and in BF16 / FP16 with rounding to nearest and with
+    stochastic rounding.  Each run samples u every `every` steps and averages
+    U(y) and the Reynolds stresses over x, z and the samples; each is compared
+    with the FP32 run."""
+    from paper_2401_17074_b300 import workloads as W
+    from paper_2401_17074_b300.channel_stats import ChannelStats, profile_errors
+    prm = W.channel_params()
+    dims, tau = prm["dims"], prm["tau"]
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    s = T.Solver(dims, tau, force=prm["force"], bc=prm["bc"], stream=stream.cuda_stream)
+    s.init_moments(*W.channel_transition_state(prm, seed=2))
+    history = []
+    t = 0
+    code = T.TSLB_OK
+    while t < warm:
+        s.step(check)
+        t += check
+        d, code = s.diagnostics()
+        history.append({"step": t, "bulk_u": d["momentum"][0] / d["mass"], "wall_shear": d["wall_shear"],
+                        "max_speed": d["max_speed"], "status": code})
+        if code != T.TSLB_OK:
+            break
+    branch = s.get_moments()
+    s.close()
+    out = {"workload": "turbulent channel %dx%dx%d from a disturbed state, FP32 for %d steps, then runs of %d steps "
+                       "sampled every %d" % (nx, ny, nz, warm, window, every),
+           "u_tau": prm["u_tau"], "u_tau_sq": prm["u_tau"] ** 2, "history": history}
+    if code != T.TSLB_OK:
+        out["error"] = "the FP32 run became unstable"
+        return out
+    u_dev = torch.empty((3, N), dtype=torch.float64, device="cuda")
+    pi_ref = W.pi_reference(branch)
+    runs = {}
+    for run in ("fp32", "fp32_perturbed", "bf16", "fp16", "bf16_sr", "fp16_sr"):
+        prec = run.split("_")[0]
+        s = T.Solver(dims, tau, force=prm["force"], bc=prm["bc"], precision=PREC_CODE[prec], stream=stream.cuda_stream,
+                     u_ref=0.05, pi_ref=pi_ref, rounding="stochastic" if run.endswith("_sr") else "nearest",
+                     rounding_seed=1)
+        rho, u, pi = branch
+        if run == "fp32_perturbed":
+            u = u * (1.0 + 1e-7 * np.random.default_rng(9).uniform(-1.0, 1.0, u.shape))
+        s.init_moments(rho, u, pi)
+        st = ChannelStats(dims)
+        for k in range(window // every):
+            s.step(every)
+            T.tslb_get_moments(s.handle, None, u_dev, None, T.DEVICE)
+            st.add(u_dev)
+        d, c = s.diagnostics()
+        s.close()
+        runs[run] = (st.result(), c, d["momentum"][0] / d["mass"])
+    del u_dev
+    torch.cuda.empty_cache()
+    ref = runs["fp32"][0]
+    yv = np.arange(1, ny - 1, dtype=np.float64)
+    nu = (tau - 0.5) / 3.0
+    # total shear stress of a stationary channel: -<u'v'> + nu dU/dy = u_tau^2 (y_c - y)/H
+    dU = np.gradient(ref["U"], yv)
+    total = -ref["uv"] + nu * dU
+    yc, H = 0.5 * (ny - 1), prm["H"]
+    linear = prm["u_tau"] ** 2 * (yc - yv) / H
+    out.update({
+        "fp32": {"U_max": float(ref["U"].max()), "uu_max": float(ref["uu"].max()), "vv_max": float(ref["vv"].max()),
+                 "ww_max": float(ref["ww"].max()), "uv_absmax": float(np.abs(ref["uv"]).max()),
+                 "bulk_u_end": runs["fp32"][2],
+                 "total_stress_vs_linear_rel_l2": float(np.linalg.norm(total - linear) / np.linalg.norm(linear)),
+                 "profiles": {k: [float(v) for v in ref[k]] for k in ("U", "uu", "vv", "ww", "uv")}},
+        "status": {k: v[1] for k, v in runs.items()},
+        "bulk_u_end": {k: v[2] for k, v in runs.items()},
+        "seconds": time.perf_counter() - t0})
+    for run in ("fp32_perturbed", "bf16", "fp16", "bf16_sr", "fp16_sr"):
+        out[run + "_vs_fp32"] = profile_errors(runs[run][0], ref)
+    return out
+
+
 def time_jet_paper(T, torch, stream, steps=200, warmup=20):
     """The paper's jet set-up at its own size (440 x 440 x 600, periodic crossflow,
     Gaussian inflow noise, sponge layer), from the paper's initial state (fluid at
@@ -622,6 +707,11 @@ def main():
     T.load()
     if args.only == "adjoint":
         line = time_adjoint(T, torch, torch.cuda.Stream())
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    if args.only == "precision-study":
+        line = turbulent_precision_study(T, torch, warm=args.warm, window=args.window)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

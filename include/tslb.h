@@ -126,7 +126,8 @@ typedef enum tslb_rounding { TSLB_ROUND_NEAREST = 0, TSLB_ROUND_STOCHASTIC = 1 }
 typedef enum tslb_kernel {
     TSLB_KERNEL_AUTO = 0,     /* the fastest kernel that supports the configuration */
     TSLB_KERNEL_DIRECT = 1,   /* one thread per node, 27 direct gathers (cross-check path) */
-    TSLB_KERNEL_FACTORED = 2  /* sum-factorised, z-marching tiled kernel */
+    TSLB_KERNEL_FACTORED = 2  /* sum-factorised, z-marching tiled kernel; up to 2^32 - 1 interior nodes
+                                 (AUTO takes the direct kernel beyond) */
 } tslb_kernel;
 
 /* Inflow noise of the round jet (Sec. 3.2). */

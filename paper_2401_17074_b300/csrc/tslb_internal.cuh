@@ -279,6 +279,21 @@ struct NodeIO {
         reinterpret_cast<uint2*>(b + 4 * fs)[n] = make_uint2(pack(m[F_PXX], m[F_PYY]), pack(m[F_PZZ], m[F_PXY]));
         reinterpret_cast<unsigned*>(b + 8 * fs)[n] = pack(m[F_PXZ], m[F_PYZ]);
     }
+    // store_rawpi where `pred` holds, as predicated stores (no branch)
+    static __device__ __forceinline__ void store_rawpi_if(T* __restrict__ b, long long fs, long long n,
+                                                          const Physics& p, const float m[NFIELDS], bool pred) {
+        const uint2 w0 = v0_word(n, p, m);
+        const uint2 w1 = make_uint2(pack(m[F_PXX], m[F_PYY]), pack(m[F_PZZ], m[F_PXY]));
+        const unsigned w2 = pack(m[F_PXZ], m[F_PYZ]);
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+            "@q st.global.v2.b32 [%1], {%4, %5};\n\t"
+            "@q st.global.v2.b32 [%2], {%6, %7};\n\t"
+            "@q st.global.b32 [%3], %8;\n\t}" ::"r"((unsigned)pred),
+            "l"(reinterpret_cast<uint2*>(b) + n), "l"(reinterpret_cast<uint2*>(b + 4 * fs) + n),
+            "l"(reinterpret_cast<unsigned*>(b + 8 * fs) + n), "r"(w0.x), "r"(w0.y), "r"(w1.x), "r"(w1.y), "r"(w2)
+            : "memory");
+    }
     static __device__ __forceinline__ void store(T* __restrict__ b, long long fs, long long n, const Physics& p,
                                                  const float m[NFIELDS]) {
         const float ip = p.inv_s_pi;
@@ -330,6 +345,19 @@ struct NodeIO<CodecF32> {
     static __device__ __forceinline__ void store_rawpi(float* __restrict__ b, long long fs, long long n,
                                                        const Physics& p, const float m[NFIELDS]) {
         store(b, fs, n, p, m);
+    }
+    // store where `pred` holds, as predicated stores (no branch)
+    static __device__ __forceinline__ void store_rawpi_if(float* __restrict__ b, long long fs, long long n,
+                                                          const Physics&, const float m[NFIELDS], bool pred) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+            "@q st.global.v4.f32 [%1], {%4, %5, %6, %7};\n\t"
+            "@q st.global.v4.f32 [%2], {%8, %9, %10, %11};\n\t"
+            "@q st.global.v2.f32 [%3], {%12, %13};\n\t}" ::"r"((unsigned)pred),
+            "l"(reinterpret_cast<float4*>(b) + n), "l"(reinterpret_cast<float4*>(b + 4 * fs) + n),
+            "l"(reinterpret_cast<float2*>(b + 8 * fs) + n), "f"(m[F_UX]), "f"(m[F_UY]), "f"(m[F_UZ]), "f"(m[F_DRHO]),
+            "f"(m[F_PXX]), "f"(m[F_PYY]), "f"(m[F_PZZ]), "f"(m[F_PXY]), "f"(m[F_PXZ]), "f"(m[F_PYZ])
+            : "memory");
     }
     static __device__ __forceinline__ void store(float* __restrict__ b, long long fs, long long n, const Physics&,
                                                  const float m[NFIELDS]) {

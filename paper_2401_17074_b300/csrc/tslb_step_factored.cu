@@ -610,8 +610,11 @@ struct Kernel {
                     load_force(p, g, oidx, G0, G1, G2);
                     guo_finish(out, G0, G1, G2, sizeof(T) == 4 ? 1.0f : p.inv_s_pi);
                 }
-                if (c.store && TSLB_IN_RANGE(oidx, g.plane * g.nz, p.err))
-                    NodeIO<Codec>::store_rawpi(dst, g.fstride, oidx, p, out);
+                // predicated, not branched: only the halo lanes (and lanes
+                // beyond the lattice) skip it, and their index is still a
+                // valid node (wrapped or clamped column)
+                NodeIO<Codec>::store_rawpi_if(dst, g.fstride, oidx, p, out,
+                                              c.store && TSLB_IN_RANGE(oidx, g.plane * g.nz, p.err));
             }
         }
         // ---- advance the z window --------------------------------------------
@@ -859,8 +862,11 @@ cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Phys
 }  // namespace
 
 bool factored_supports(const tslb_s* h) {
-    // 32-bit node offsets inside a field
-    return (long long)h->g.plane * h->g.nz < (1LL << 31);
+    // node offsets inside a field are unsigned 32-bit (n = col + plane * z, and
+    // every byte offset is formed in 64 bits from it): up to 2^32 - 1 nodes,
+    // which covers FP32 storage up to the device's memory (80 bytes per node
+    // for the two buffers) and 16-bit storage up to 4.29 G nodes
+    return (long long)h->g.plane * h->g.nz < (1LL << 32);
 }
 
 cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p) {

@@ -240,3 +240,88 @@ def divfree_random(n=128, u_rms=0.02, kmax=8, tau=0.52, seed=5):
     # arrays are indexed [z][y][x] already (meshgrid ij over z, y, x)
     rho = np.ones(n ** 3)
     return (n, n, n), _pack(rho, [ua.reshape(-1) for ua in u], [p.reshape(-1) for p in pi])
+
+
+def _hash32(xp, k):
+    """Integer hash of non-negative int64 values below 2^32 (two xorshift-multiply
+    rounds with a multiplier below 2^31, so every product fits in int64); exact
+    and identical for numpy arrays and torch tensors."""
+    M = 0xFFFFFFFF
+    k = ((k ^ (k >> 16)) * 0x45D9F3B) & M
+    k = ((k ^ (k >> 16)) * 0x45D9F3B) & M
+    return k ^ (k >> 16)
+
+
+def hashed_moments(idx, seed, drho=2.0 ** -7, du=2.0 ** -5, dpi=2.0 ** -10):
+    """Random moments at lattice node indices idx (int64 array, numpy or torch):
+    rho - 1, u and Pi^neq from a counter hash of (idx, field, seed), uniform in
+    [-amp, amp) with power-of-two amplitudes.  Every value is a multiple of
+    2^-23 times its amplitude, so it is exact in FP32 and numpy and torch give
+    identical bits.  Returns (drho [n], u [3, n], pi [6, n]) in FP32, for
+    lattices too large to build on the host."""
+    is_torch = type(idx).__module__.startswith("torch")
+    out = []
+    for f in range(10):
+        key = (idx * 10 + f + 1000003 * seed) & 0xFFFFFFFF
+        h = _hash32(None, key)
+        q = (h >> 8) - (1 << 23)  # integer in [-2^23, 2^23)
+        amp = drho if f == 0 else (du if f < 4 else dpi)
+        scale = amp * 2.0 ** -23  # a power of two: q * scale is exact in FP32
+        if is_torch:
+            import torch
+            out.append(q.to(torch.float32) * scale)
+        else:
+            out.append(q.astype(np.float32) * np.float32(scale))
+    if is_torch:
+        import torch
+        return out[0], torch.stack(out[1:4]), torch.stack(out[4:])
+    return out[0], np.stack(out[1:4]), np.stack(out[4:])
+
+
+def channel_transition_state(prm, seed=2, streak=0.15, vortex=0.04, noise=0.03):
+    """A disturbed channel flow that becomes turbulent quickly.
+
+    Mean flow: Reichardt's smooth law of the wall for the Re_tau of the set-up
+    (u+ = ln(1 + 0.4 y+)/0.4 + 7.8 (1 - exp(-y+/11) - (y+/11) exp(-y+/3)),
+    y+ the distance to the nearer wall in wall units u_tau/nu).  On it:
+    streamwise streaks u' = streak U_c sin(beta z) s(y) cos(alpha x) and
+    streamwise vortices from the stream function psi = vortex U_c s(y)^2 / beta
+    cos(beta z) (v = d psi/dz, w = -d psi/dy, divergence-free), with spanwise
+    period 100 wall units and streamwise period nx, s(y) = sin(pi eta), eta
+    the fraction of the way across the channel; plus noise U_c xi, xi ~ U(-1,1)
+    seeded, on every component.  rho = 1 and Pi^neq from the mean shear."""
+    nx, ny, nz = prm["dims"]
+    H, tau, ut = prm["H"], prm["tau"], prm["u_tau"]
+    nu = CS2 * (tau - 0.5)
+    y0, y1 = 0.5, ny - 1.5
+    yv = np.arange(ny, dtype=np.float64)
+    dw = np.minimum(yv - y0, y1 - yv)  # distance to the nearer wall
+    yp = np.maximum(dw, 0.0) * ut / nu
+    up = np.log1p(0.4 * yp) / 0.4 + 7.8 * (1 - np.exp(-yp / 11) - (yp / 11) * np.exp(-yp / 3))
+    U = ut * up
+    Uc = float(U.max())
+    dU = np.gradient(U, yv)
+    fluid = (yv >= 1) & (yv <= ny - 2)
+    U[~fluid] = 0.0
+    dU[~fluid] = 0.0
+    eta = np.clip((yv - y0) / (y1 - y0), 0.0, 1.0)
+    s = np.sin(math.pi * eta)
+    ds = math.pi / (y1 - y0) * np.cos(math.pi * eta)
+    beta = 2 * math.pi / max(8.0, 100.0 * nu / ut)
+    beta = 2 * math.pi / (nz / max(1, round(nz * beta / (2 * math.pi))))  # whole periods in z
+    alpha = 2 * math.pi / nx
+    z, y, x = np.meshgrid(np.arange(nz), yv, np.arange(nx), indexing="ij")
+    S, dS = s[y.astype(int)], ds[y.astype(int)]
+    ux = U[y.astype(int)] + streak * Uc * np.sin(beta * z) * S * np.cos(alpha * x)
+    uy = vortex * Uc * (-np.sin(beta * z)) * S * S
+    uz = -vortex * Uc / beta * np.cos(beta * z) * 2 * S * dS
+    rng = np.random.default_rng(seed)
+    u = [ux.reshape(-1), uy.reshape(-1), uz.reshape(-1)]
+    mask = np.broadcast_to(fluid[None, :, None], (nz, ny, nx)).reshape(-1)
+    for a in range(3):
+        u[a] = u[a] + noise * Uc * rng.uniform(-1.0, 1.0, u[a].size)
+        u[a][~mask] = 0.0
+    N = nx * ny * nz
+    pxy = np.broadcast_to((-CS2 * tau * dU)[None, :, None], (nz, ny, nx)).reshape(-1).copy()
+    zero = np.zeros(N)
+    return np.ones(N), np.stack(u), np.stack([zero, zero, zero, pxy, zero, zero])

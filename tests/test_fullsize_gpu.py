@@ -215,3 +215,60 @@ def test_paper_jet_full_size_sampled(cuda_ok):
     pairs = [_compare_column(out, (rho, u, pi), dims, prm["tau"], prm["force"], prm["bc"], c, inflow=prm["inflow"],
                              sponge=prm["sponge"]) for c in cols]
     _check(pairs, 3e-6)
+
+
+def test_bf16_lattice_beyond_2_31_nodes(cuda_ok):
+    """A BF16 lattice of 1024 x 1024 x 2049 = 2,148,532,224 nodes (more than
+    2^31; 86 GB for the two moment buffers) runs the factored kernel, and three
+    sampled z columns after two steps match the oracle on their cut-out boxes:
+    (0, 0), whose layer z = 2048 starts at node 2^31, (1023, 1023), which
+    ends at node 2^31 - 1 in layer 2047, and one inside.  The input is the
+    counter-hashed random state (exact in FP32 on both sides), built on the
+    device in chunks.  Bounds as for 16-bit storage elsewhere: u 4 units of
+    BF16 roundoff, Pi 16 (relative L2 over the column)."""
+    import torch
+    dims = (1024, 1024, 2049)
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    assert N > 2 ** 31
+    free, _ = torch.cuda.mem_get_info()
+    if free < 200e9:
+        pytest.skip("needs about 180 GB of free device memory")
+    tau, seed = 0.6, 7
+    s = T.Solver(dims, tau, precision=T.BF16, u_ref=0.05, pi_ref=2.0 ** -9, kernel=T.KERNEL_FACTORED)
+    dev = "cuda"
+    drho = torch.empty(N, dtype=torch.float32, device=dev)
+    u = torch.empty((3, N), dtype=torch.float32, device=dev)
+    pi = torch.empty((6, N), dtype=torch.float32, device=dev)
+    chunk = nx * ny * 64
+    for a in range(0, N, chunk):
+        b = min(N, a + chunk)
+        r0, u0, p0 = W.hashed_moments(torch.arange(a, b, dtype=torch.int64, device=dev), seed)
+        drho[a:b] = r0
+        u[:, a:b] = u0
+        pi[:, a:b] = p0
+    T.tslb_init_moments_f32(s.handle, drho, u, pi)
+    s.step(NSTEPS)
+    T.tslb_get_moments_f32(s.handle, drho, u, pi, T.DEVICE)
+    torch.cuda.synchronize()
+    s.close()
+    R = NSTEPS
+    ur = 2.0 ** -8  # BF16 unit roundoff
+    for cx, cy in ((0, 0), (nx - 1, ny - 1), (511, 700)):
+        xs = [(cx + d) % nx for d in range(-R, R + 1)]
+        ys = [(cy + d) % ny for d in range(-R, R + 1)]
+        zz, yy, xx = np.meshgrid(np.arange(nz), ys, xs, indexing="ij")
+        gidx = (xx + nx * (yy + ny * zz)).reshape(-1).astype(np.int64)
+        r0, u0, p0 = W.hashed_moments(gidx, seed)
+        o = oracle.OracleSim((len(xs), len(ys), nz), tau)
+        o.init_moments(1.0 + r0.astype(np.float64), u0.astype(np.float64), p0.astype(np.float64))
+        o.step(NSTEPS)
+        r, uu, pp = o.get_moments()
+        ref = np.concatenate([(r - 1)[None], uu, pp]).reshape(10, nz, len(ys), len(xs))[:, :, R, R]
+        col = torch.as_tensor(cx + nx * (cy + ny * np.arange(nz, dtype=np.int64)), device=dev)
+        got = torch.cat([drho[col][None], u[:, col], pi[:, col]]).double().cpu().numpy()
+        eu = np.linalg.norm(got[1:4] - ref[1:4]) / np.linalg.norm(ref[1:4])
+        ep = np.linalg.norm(got[4:] - ref[4:]) / np.linalg.norm(ref[4:])
+        er = np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[0])
+        print("column (%d, %d): drho %.2e u %.2e Pi %.2e" % (cx, cy, er, eu, ep))
+        assert eu <= 4 * ur and er <= 4 * ur and ep <= 16 * ur, (cx, cy, er, eu, ep)
