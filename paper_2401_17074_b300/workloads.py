@@ -278,18 +278,25 @@ def hashed_moments(idx, seed, drho=2.0 ** -7, du=2.0 ** -5, dpi=2.0 ** -10):
     return out[0], np.stack(out[1:4]), np.stack(out[4:])
 
 
-def channel_transition_state(prm, seed=2, streak=0.15, vortex=0.04, noise=0.03):
-    """A disturbed channel flow that becomes turbulent quickly.
+def channel_transition_state(prm, seed=2, streak=0.3, vortex=0.3, modes=0.1, noise=0.02):
+    """A strongly disturbed channel flow meant to become turbulent quickly.
 
     Mean flow: Reichardt's smooth law of the wall for the Re_tau of the set-up
     (u+ = ln(1 + 0.4 y+)/0.4 + 7.8 (1 - exp(-y+/11) - (y+/11) exp(-y+/3)),
-    y+ the distance to the nearer wall in wall units u_tau/nu).  On it:
-    streamwise streaks u' = streak U_c sin(beta z) s(y) cos(alpha x) and
-    streamwise vortices from the stream function psi = vortex U_c s(y)^2 / beta
-    cos(beta z) (v = d psi/dz, w = -d psi/dy, divergence-free), with spanwise
-    period 100 wall units and streamwise period nx, s(y) = sin(pi eta), eta
-    the fraction of the way across the channel; plus noise U_c xi, xi ~ U(-1,1)
-    seeded, on every component.  rho = 1 and Pi^neq from the mean shear."""
+    y+ the distance to the nearer wall in wall units u_tau/nu).  On it, with
+    s(y) = sin(pi eta), eta the fraction of the way across the channel, and
+    U_c the centreline velocity:
+      - streamwise streaks u' = streak U_c sin(beta z) s(y) cos(alpha x);
+      - streamwise vortices from the stream function
+        psi = vortex U_c s(y)^2 / beta cos(beta z), v = d psi/dz, w = -d psi/dy,
+        both modulated along x by (1 + 0.5 cos(2 alpha x)) (still divergence-free
+        in every x plane);
+      - eight random large-scale modes per component, s(y) sin(k_x x + k_z z + phi)
+        with k_x, k_z of 1 to 4 periods, of total amplitude `modes` U_c;
+      - noise U_c xi, xi ~ U(-1, 1), on every component.
+    beta gives a spanwise period near 100 wall units (a whole number of
+    periods in z), alpha one period along x.  rho = 1 and Pi^neq from the mean
+    shear.  Seeded."""
     nx, ny, nz = prm["dims"]
     H, tau, ut = prm["H"], prm["tau"], prm["u_tau"]
     nu = CS2 * (tau - 0.5)
@@ -307,16 +314,23 @@ def channel_transition_state(prm, seed=2, streak=0.15, vortex=0.04, noise=0.03):
     eta = np.clip((yv - y0) / (y1 - y0), 0.0, 1.0)
     s = np.sin(math.pi * eta)
     ds = math.pi / (y1 - y0) * np.cos(math.pi * eta)
-    beta = 2 * math.pi / max(8.0, 100.0 * nu / ut)
-    beta = 2 * math.pi / (nz / max(1, round(nz * beta / (2 * math.pi))))  # whole periods in z
+    nper = max(1, round(nz * ut / (100.0 * nu)))  # spanwise periods of about 100 wall units
+    beta = 2 * math.pi * nper / nz
     alpha = 2 * math.pi / nx
-    z, y, x = np.meshgrid(np.arange(nz), yv, np.arange(nx), indexing="ij")
-    S, dS = s[y.astype(int)], ds[y.astype(int)]
-    ux = U[y.astype(int)] + streak * Uc * np.sin(beta * z) * S * np.cos(alpha * x)
-    uy = vortex * Uc * (-np.sin(beta * z)) * S * S
-    uz = -vortex * Uc / beta * np.cos(beta * z) * 2 * S * dS
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    S, dS = s[y], ds[y]
+    fx = 1.0 + 0.5 * np.cos(2 * alpha * x)
+    ux = U[y] + streak * Uc * np.sin(beta * z) * S * np.cos(alpha * x)
+    uy = -vortex * Uc * np.sin(beta * z) * S * S * fx
+    uz = -vortex * Uc / beta * np.cos(beta * z) * 2 * S * dS * fx
     rng = np.random.default_rng(seed)
-    u = [ux.reshape(-1), uy.reshape(-1), uz.reshape(-1)]
+    u = [ux, uy, uz]
+    for a in range(3):
+        for _ in range(8):
+            kx = 2 * math.pi * rng.integers(1, 5) / nx
+            kz = 2 * math.pi * rng.integers(1, 5) / nz
+            u[a] = u[a] + (modes / 8.0) * Uc * S * np.sin(kx * x + kz * z + rng.uniform(0, 2 * math.pi))
+    u = [c.reshape(-1) for c in u]
     mask = np.broadcast_to(fluid[None, :, None], (nz, ny, nx)).reshape(-1)
     for a in range(3):
         u[a] = u[a] + noise * Uc * rng.uniform(-1.0, 1.0, u[a].size)
