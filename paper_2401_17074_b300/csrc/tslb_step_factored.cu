@@ -349,7 +349,7 @@ template <bool HOIST>
 __device__ __forceinline__ bool role(bool v) { return HOIST ? v : uni(v); }
 
 // March specialisations by warp role (see Kernel::march).
-constexpr int ROLE_ANY = 0, ROLE_PLAIN = 1;
+constexpr int ROLE_ANY = 0, ROLE_PLAIN = 1, ROLE_WALL = 2;
 
 // Per-thread constants of the march.
 struct Ctx {
@@ -424,7 +424,9 @@ struct Kernel {
     // STEADY: 2 <= j <= np - 3, so the plane and the next one are stored
     // interior planes inside the chunk (no wrap, no ghost, exchange active).
     // ROLE: ROLE_PLAIN for an output row with no wall, ghost or NEE role (its
-    // role tests are compile-time constants), ROLE_ANY for the others (tests
+    // role tests are compile-time constants), ROLE_WALL for an output row next
+    // to a bounce-back wall and nothing else (only the wall correction is
+    // tested, per side), ROLE_ANY for the others (tests
     // at run time on the warp's role flags).
     template <int PAR, bool STEADY, int ROLE>
     static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
@@ -519,11 +521,11 @@ struct Kernel {
             {
                 const unsigned par = (unsigned)((j - 2) >> 1) & 1u;  // phase of this buffer's (j-2)/2-th use
                 // plain rows (warps 1 .. WROWS - 2) always have both neighbours
-                if (ROLE == ROLE_PLAIN || c.wait_lo) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
-                if (ROLE == ROLE_PLAIN || c.wait_hi) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
+                if (ROLE != ROLE_ANY || c.wait_lo) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
+                if (ROLE != ROLE_ANY || c.wait_hi) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
             }
             // halo and ghost rows only feed the y exchange (warp-uniform)
-            if (ROLE == ROLE_PLAIN || role<HOIST>(c.out_row)) {
+            if (ROLE != ROLE_ANY || role<HOIST>(c.out_row)) {
                 // L / R: (r = 0, r = 1) pairs per k1 and the r = 2 scalars
                 f2 LA[3], RA[3];
                 float Ls[3], Rs[3];
@@ -574,7 +576,7 @@ struct Kernel {
                 // ---- halfway bounce-back on the wall-adjacent rows ----------
                 // The ghost row next to the wall computed the correction for
                 // this plane one march step earlier (see bounce_back_correction).
-                if (ROLE == ROLE_ANY && c.ybb) {
+                if (ROLE == ROLE_WALL || (ROLE == ROLE_ANY && c.ybb)) {
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
                         if (!role<HOIST>(side == 0 ? c.row_lo : c.row_hi)) continue;
@@ -784,11 +786,20 @@ __global__ void __launch_bounds__(NT, 1)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     K::template prefetch<0>(c, g, p, src, pfb, 0);
     // Output rows without a wall, ghost or NEE role (warp-uniform) run the
-    // march with those tests compiled out; the halo, ghost and wall rows run
-    // the general one.
+    // march with those tests compiled out, rows next to a bounce-back wall one
+    // with only the wall correction; the halo, ghost and NEE rows run the
+    // general one.
     const bool plain = uni(c.warp >= 1 && c.warp <= YOUT && c.out_row && !c.zero_row && !c.nee_row &&
                            !(c.ybb && (c.row_lo || c.row_hi)));
+    // (the wall march exists only in the 16-bit variants that can have
+    // bounce-back walls -- periodic x, no NEE walls, no sponge: BF16 channel
+    // 66.5 -> 68.1 GLUPS; with FP32 storage the third march made the kernel
+    // spill and measured 1.2 % slower, so FP32 keeps two)
+    constexpr bool WALLS = !XFREE && !NEEY && !SPONGE && sizeof(typename K::T) != 4;
+    const bool wall = WALLS && uni(c.warp >= 1 && c.warp <= YOUT && c.out_row && !c.zero_row && !c.nee_row &&
+                                   c.ybb && (c.row_lo || c.row_hi));
     if (plain) K::template march<ROLE_PLAIN>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
+    else if (WALLS && wall) K::template march<WALLS ? ROLE_WALL : ROLE_ANY>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
     else K::template march<ROLE_ANY>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
 }
 
