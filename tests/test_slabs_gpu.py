@@ -86,3 +86,33 @@ def test_halo_slab_rejects_unsupported(cuda_ok):
         s.set_force_field(np.zeros((3, 12 * 7 * 6), dtype=np.float32))
     assert ei.value.code == T.TSLB_ERR_UNSUPPORTED
     s.close()
+
+
+def test_slab_chain_random_cases(cuda_ok):
+    """Property-based: random lattice shapes, slab counts (ragged splits),
+    y faces (periodic or bounce-back), storage types, forces and relaxation
+    times; the chain must match the single handle bit for bit after a random
+    number of steps."""
+    from hypothesis import given, settings, HealthCheck, strategies as st
+
+    @settings(max_examples=25, deadline=None, suppress_health_check=list(HealthCheck))
+    @given(nx=st.integers(3, 45), ny=st.integers(4, 36), nslabs=st.integers(2, 5), extra=st.integers(0, 7),
+           walls=st.booleans(), prec=st.sampled_from([T.FP32, T.BF16, T.FP16]), tau=st.floats(0.51, 1.5),
+           steps=st.integers(1, 9), seed=st.integers(0, 10 ** 6))
+    def run(nx, ny, nslabs, extra, walls, prec, tau, steps, seed):
+        nz = 3 * nslabs + extra
+        dims = (nx, ny, nz)
+        bc = (0, 0, 1, 1, 0, 0) if walls else (0,) * 6
+        state = W.random_state(dims, seed=seed, drho=0.005, du=0.02, dpi=2e-4)
+        force = (1e-5, -2e-6, 3e-6)
+        kw = {} if prec == T.FP32 else dict(precision=prec, u_ref=0.05, pi_ref=W.pi_reference(state))
+        ref = _single(dims, tau, force, bc, state, steps, **kw)
+        chain = SlabChain(dims, tau, nslabs, force=force, bc=bc, **kw)
+        chain.init_moments(*state)
+        chain.step(steps)
+        got = chain.get_moments()
+        chain.close()
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+
+    run()
