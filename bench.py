@@ -488,6 +488,39 @@ def turbulent_precision_study(T, torch, warm=300000, window=100000, every=1000, 
     return out
 
 
+def time_jet(T, torch, stream, precision="fp32", steps=200, warmup=20):
+    """The round jet of the benchmark set-up (256 x 256 x 640: NEE inflow with a
+    D = 20 nozzle and 1 % uniform noise, zero-gradient outflow, free-slip sides),
+    from rest, built on the device; the default kernel."""
+    from paper_2401_17074_b300 import workloads as W
+    prm = W.jet_params()
+    dims = prm["dims"]
+    N = dims[0] * dims[1] * dims[2]
+    s = T.Solver(dims, prm["tau"], force=prm["force"], bc=prm["bc"], inflow=prm["inflow"],
+                 precision=PREC_CODE[precision], u_ref=0.05, pi_ref=1e-3, stream=stream.cuda_stream)
+    rho = torch.ones(N, dtype=torch.float64, device="cuda")
+    zeros = torch.zeros((9, N), dtype=torch.float64, device="cuda")
+    s.init_moments(rho, zeros[0:3], zeros[3:9])
+    del rho, zeros
+    s.step(warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    d, code = s.diagnostics()
+    nodes = s.interior_nodes()
+    s.close()
+    torch.cuda.empty_cache()
+    return {"workload": "round jet %dx%dx%d: NEE inflow (D = 20, 1 %% uniform noise), outflow, free-slip sides; "
+                        "%s storage" % (dims + (precision,)),
+            "value": job_mlups(nodes, 1, steps, ms), "unit": "MLUPS", "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "interior_nodes": nodes, "max_speed": d["max_speed"], "status": code}
+
+
 def time_jet_paper(T, torch, stream, steps=200, warmup=20):
     """The paper's jet set-up at its own size (440 x 440 x 600, periodic crossflow,
     Gaussian inflow noise, sponge layer), from the paper's initial state (fluid at
@@ -782,6 +815,8 @@ def main():
                                                                            args.precision),
                      "value": job_mlups(nn, 1, k_nee, msn), "unit": "MLUPS", "steps": k_nee,
                      "ms_per_step": msn / k_nee, "status": cn},
+                 "jet": time_jet(T, torch, stream),
+                 "jet_bf16": time_jet(T, torch, stream, precision="bf16"),
                  "jet_paper": time_jet_paper(T, torch, stream),
                  "pressure_driven_300M": time_pressure_driven(T, torch, stream),
                  "d2q9_channel": time_channel2d(T, torch, stream, hbm)}

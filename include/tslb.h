@@ -174,6 +174,11 @@ typedef struct tslb_options {
     int forcing;          /* tslb_forcing, default TSLB_FORCING_LUO */
     int rounding;         /* tslb_rounding, default TSLB_ROUND_NEAREST */
     uint64_t rounding_seed; /* key of the stochastic rounding bits, default 0 */
+    /* Halo slabs only: cudaStream_t on which tslb_halo_export / tslb_halo_import
+     * run (NULL = the handle's stream, default).  With a separate stream the
+     * library orders the copies against the steps with events, so an exchange
+     * can overlap a split step's interior part (tslb_step_part). */
+    void* halo_stream;
 } tslb_options;
 
 typedef struct tslb_diag {
@@ -326,10 +331,31 @@ int tslb_diagnostics_noalloc(const double* rho, const double* u, const double* p
  * handle's stream (device buffers) or complete before returning (host
  * buffers); a device buffer shared by two handles on different streams must
  * be ordered between them by the caller (an event, or one shared stream).
- * All three return TSLB_ERR_STATE on a handle without TSLB_BC_HALO faces. */
+ * With options.halo_stream set, both run on that stream and the library
+ * orders them against the steps with events: an export waits for the layers
+ * it reads (the last step, or an open step's edges), an import for the last
+ * step or open step's edges that read the ghosts it overwrites, and the next
+ * step (or EDGES part) waits for the imports.  The caller then orders its
+ * buffers with respect to that stream only.
+ * These calls return TSLB_ERR_STATE on a handle without TSLB_BC_HALO faces. */
 
 /* Bytes of one packed plane. */
 int tslb_halo_plane_bytes(const tslb_t* h, int64_t* bytes);
+
+/* A step of a halo slab in two parts, so that the exchange of its boundary
+ * layers can overlap the update of the rest:
+ *   TSLB_PART_EDGES    advances the layers z < e and z >= nz - e
+ *                      (e = TSLB_HALO_EDGE_LAYERS, or all layers when nz <= 2e);
+ *   TSLB_PART_INTERIOR advances the layers in between and completes the step.
+ * Between the two the step is open: tslb_halo_export exports the layers z = 0
+ * and z = nz - 1 of the state being produced (already final), and
+ * tslb_halo_import loads the ghosts of the next step (the open step's edges
+ * no longer read them).  EDGES then INTERIOR equals one tslb_step bit for bit.
+ * TSLB_ERR_STATE for EDGES while a step is open, INTERIOR while none is, or
+ * tslb_step while one is; TSLB_ERR_STATE on a handle without halo faces. */
+enum { TSLB_PART_EDGES = 1, TSLB_PART_INTERIOR = 2 };
+#define TSLB_HALO_EDGE_LAYERS 4
+int tslb_step_part(tslb_t* h, int part);
 
 /* Copy this slab's boundary layer -- side 0: z = 0, side 1: z = nz - 1, at the
  * current step -- into dst as one packed plane (host or device per `where`). */

@@ -35,8 +35,10 @@ EXPORTED = [
     "tslb_options_default", "tslb_create", "tslb_init_moments", "tslb_init_moments_f32", "tslb_set_force_field",
     "tslb_step", "tslb_get_moments", "tslb_get_moments_f32", "tslb_diagnostics", "tslb_adjoint_force_gradient",
     "tslb_adjoint", "tslb_interior_nodes", "tslb_synchronize", "tslb_destroy", "tslb_last_error",
-    "tslb_diagnostics_noalloc", "tslb_halo_plane_bytes", "tslb_halo_export", "tslb_halo_import",
+    "tslb_diagnostics_noalloc", "tslb_halo_plane_bytes", "tslb_halo_export", "tslb_halo_import", "tslb_step_part",
 ]
+TSLB_PART_EDGES, TSLB_PART_INTERIOR = 1, 2
+HALO_EDGE_LAYERS = 4
 NOALLOC_MAX_NODES = 1 << 26
 
 
@@ -50,7 +52,7 @@ class tslb_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("checkpoint_every", ctypes.c_int), ("inflow", tslb_inflow), ("sponge_width", ctypes.c_int),
                 ("sponge_k", ctypes.c_double), ("forcing", ctypes.c_int), ("rounding", ctypes.c_int),
-                ("rounding_seed", ctypes.c_uint64)]
+                ("rounding_seed", ctypes.c_uint64), ("halo_stream", ctypes.c_void_p)]
 
 
 class tslb_diag(ctypes.Structure):
@@ -111,6 +113,7 @@ def load(build_if_missing=True):
     L.tslb_halo_plane_bytes.argtypes = [vp, ctypes.POINTER(i64)]
     L.tslb_halo_export.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.tslb_halo_import.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.tslb_step_part.argtypes = [vp, ctypes.c_int]
     _lib = L
     return L
 
@@ -300,11 +303,13 @@ def tslb_halo_plane_bytes(h):
 
 
 def _buf_ptr(a):
-    """(pointer, where) of a contiguous buffer: CUDA tensor, CPU tensor or numpy array."""
+    """(pointer, where) of a contiguous buffer: CUDA tensor, CPU tensor or numpy array.
+    A CUDA buffer is passed as it is, without draining PyTorch's stream: halo
+    buffers are ordered by the caller on the handle's halo stream."""
     if hasattr(a, "is_cuda") and a.is_cuda:
         if not a.is_contiguous():
             raise ValueError("halo buffers must be contiguous")
-        return _device_ptr(a), DEVICE
+        return ctypes.c_void_p(a.data_ptr()), DEVICE
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr()), HOST
     if not a.flags["C_CONTIGUOUS"]:
@@ -332,6 +337,11 @@ def tslb_halo_import(h, side, src):
     _check(load().tslb_halo_import(h, int(side), p, where), h)
 
 
+def tslb_step_part(h, part):
+    """One part of a split step of a halo slab: TSLB_PART_EDGES, then TSLB_PART_INTERIOR."""
+    _check(load().tslb_step_part(h, int(part)), h)
+
+
 def tslb_interior_nodes(h):
     return load().tslb_interior_nodes(h)
 
@@ -355,7 +365,7 @@ class Solver:
 
     def __init__(self, dims, tau, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05, pi_ref=1e-3,
                  kernel=KERNEL_AUTO, stream=None, device=0, checkpoint_every=0, inflow=None, sponge=None,
-                 lattice=None, forcing="luo", rounding="nearest", rounding_seed=0):
+                 lattice=None, forcing="luo", rounding="nearest", rounding_seed=0, halo_stream=None):
         """inflow: dict(center2, diameter, u_jet, noise_amp, seed[, noise="uniform" | "gaussian"]);
         sponge: (width, K) viscosity layer towards the z+ face (tslb_options.sponge_width / sponge_k);
         rounding: "nearest" or "stochastic" (16-bit storage; tslb_options.rounding / rounding_seed)."""
@@ -380,6 +390,8 @@ class Solver:
         o.forcing = {"luo": TSLB_FORCING_LUO, "guo": TSLB_FORCING_GUO}[forcing]
         o.rounding = {"nearest": TSLB_ROUND_NEAREST, "stochastic": TSLB_ROUND_STOCHASTIC}[rounding]
         o.rounding_seed = int(rounding_seed)
+        if halo_stream is not None:
+            o.halo_stream = ctypes.c_void_p(int(halo_stream))
         if sponge is not None:
             o.sponge_width = int(sponge[0])
             o.sponge_k = float(sponge[1])
@@ -460,6 +472,9 @@ class Solver:
 
     def halo_import(self, side, src):
         tslb_halo_import(self._h, side, src)
+
+    def step_part(self, part):
+        tslb_step_part(self._h, part)
 
     def adjoint(self, lam, nsteps):
         """dJ/dF ([3, N] FP32) for the cotangent lam = dJ/dm of the current moments,

@@ -99,6 +99,10 @@ void release(tslb_s* h) {
     if (h->adj_ws) cudaFree(h->adj_ws);
     if (h->adj_lam) cudaFree(h->adj_lam);
     if (h->ghost) cudaFree(h->ghost);
+    if (h->ev_step) cudaEventDestroy(h->ev_step);
+    if (h->ev_edges) cudaEventDestroy(h->ev_edges);
+    if (h->ev_halo) cudaEventDestroy(h->ev_halo);
+    if (h->halo_stream && h->halo_stream != h->stream) cudaStreamSynchronize(h->halo_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -137,7 +141,7 @@ Physics make_physics(const tslb_s* h) {
     p.sr_key = sr_step_key(h->rounding_seed, h->t);
     if (h->ghost) {
         p.halo[0] = h->ghost;
-        p.halo[1] = static_cast<const char*>(h->ghost) + halo_plane_bytes(h);
+        p.halo[1] = static_cast<const char*>(h->ghost) + halo_ghost_stride(h);
     }
     p.omega1_pi = (float)((1.0 - h->omega) * (double)p.s_pi);
     p.pi_store = (float)((double)p.inv_s_pi / 216.0);
@@ -192,6 +196,7 @@ int init_moments_impl(tslb_t* h, const H* rho, const H* u, const H* pi, int wher
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (!rho || !u) return fail(h, TSLB_ERR_INVALID, "rho (or drho) and u are required");
     if (where != TSLB_HOST && where != TSLB_DEVICE) return fail(h, TSLB_ERR_INVALID, "bad 'where'");
+    if (h->step_open) return fail(h, TSLB_ERR_STATE, "a split step is open");
     cudaSetDevice(h->device);
     const long long fN = h->dims[0] * h->dims[1] * h->dims[2];
     const tslb::Physics p = tslb::make_physics(h);
@@ -265,6 +270,7 @@ int tslb_options_default(tslb_options* opt) {
     opt->device = 0;
     opt->kernel = TSLB_KERNEL_AUTO;
     opt->checkpoint_every = 0;
+    opt->halo_stream = nullptr;
     return TSLB_OK;
 }
 
@@ -448,9 +454,16 @@ int tslb_create(tslb_t** out, int lattice, const int64_t dims[3], double tau, co
     }
     if (zhalo) {
         // the two ghost planes the step reads at z = -1 and z = nz (packed, rest state)
-        const size_t gb = 2 * halo_plane_bytes(h);
+        const size_t gb = 2 * halo_ghost_stride(h);
         e = dev_alloc(&h->ghost, gb);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->ghost, 0, gb, h->stream);
+        h->halo_stream = o.halo_stream ? (cudaStream_t)o.halo_stream : h->stream;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_step, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_edges, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_halo, cudaEventDisableTiming);
+        // the ghosts' rest state is written on the handle's stream: imports on
+        // another stream come after it
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_step, h->stream);
         if (e != cudaSuccess) {
             std::string m = std::string("device allocation of the ghost planes failed: ") + cudaGetErrorString(e);
             release(h);
@@ -544,6 +557,7 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
     const Range range("tslb_step");
     if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
     if (nsteps < 0) return fail(h, TSLB_ERR_INVALID, "nsteps < 0");
+    if (h->step_open) return fail(h, TSLB_ERR_STATE, "a split step is open: call tslb_step_part(TSLB_PART_INTERIOR)");
     cudaSetDevice(h->device);
     if (h->lattice == TSLB_D3Q27 && (h->kernel == TSLB_KERNEL_FACTORED || h->ghost) && !tslb::factored_supports(h))
         return fail(h, TSLB_ERR_UNSUPPORTED, "the factored kernel does not support this configuration");
@@ -563,11 +577,48 @@ int tslb_step(tslb_t* h, int64_t nsteps) {
             ++h->ckpt_valid;
         }
         const tslb::Physics p = tslb::make_physics(h);
+        const bool sep = h->ghost && h->halo_stream != h->stream;
+        if (sep) cudaStreamWaitEvent(h->stream, h->ev_halo, 0);  // the ghosts this step reads
         e = tslb::launch_step_any(h, h->buf[h->cur], h->buf[h->cur ^ 1], p);
+        if (e == cudaSuccess && sep) e = cudaEventRecord(h->ev_step, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
         h->cur ^= 1;
         h->t += 1;
     }
+    return TSLB_OK;
+}
+
+int tslb_step_part(tslb_t* h, int part) {
+    const Range range("tslb_step_part");
+    if (!valid_handle(h)) return fail(nullptr, TSLB_ERR_INVALID, "null handle");
+    if (part != TSLB_PART_EDGES && part != TSLB_PART_INTERIOR) return fail(h, TSLB_ERR_INVALID, "unknown part");
+    if (!h->ghost) return fail(h, TSLB_ERR_STATE, "split steps are for halo slabs");
+    if (part == TSLB_PART_EDGES && h->step_open) return fail(h, TSLB_ERR_STATE, "a split step is already open");
+    if (part == TSLB_PART_INTERIOR && !h->step_open) return fail(h, TSLB_ERR_STATE, "no split step is open");
+    if (!tslb::factored_supports(h)) return fail(h, TSLB_ERR_UNSUPPORTED, "lattice too large for the factored kernel");
+    cudaSetDevice(h->device);
+    const tslb::Physics p = tslb::make_physics(h);
+    const int nz = h->g.nz, ed = TSLB_HALO_EDGE_LAYERS;
+    const bool whole = nz <= 2 * ed;  // the edges are the whole slab
+    const bool sep = h->halo_stream != h->stream;
+    cudaError_t e = cudaSuccess;
+    void* src = h->buf[h->cur];
+    void* dst = h->buf[h->cur ^ 1];
+    if (part == TSLB_PART_EDGES) {
+        if (sep) e = cudaStreamWaitEvent(h->stream, h->ev_halo, 0);
+        if (e == cudaSuccess) e = tslb::launch_step_factored_range(h, src, dst, p, 0, whole ? nz : ed);
+        if (e == cudaSuccess && !whole) e = tslb::launch_step_factored_range(h, src, dst, p, nz - ed, nz);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_edges, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step launch (edges)");
+        h->step_open = true;
+        return TSLB_OK;
+    }
+    if (!whole) e = tslb::launch_step_factored_range(h, src, dst, p, ed, nz - ed);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_step, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch (interior)");
+    h->step_open = false;
+    h->cur ^= 1;
+    h->t += 1;
     return TSLB_OK;
 }
 
@@ -660,21 +711,26 @@ static int halo_copy(tslb_t* h, int side, void* other, int where, bool to_other)
     cudaSetDevice(h->device);
     const tslb::Geometry& g = h->g;
     const size_t pb = halo_plane_bytes(h), e4 = 4 * h->elem * (size_t)g.plane, e2 = 2 * h->elem * (size_t)g.plane;
-    cudaError_t e = cudaSuccess;
-    if (to_other) {
-        // layer z = 0 or nz - 1 of the current buffer -> packed [V0 | V1 | V2]
-        const char* b = static_cast<const char*>(h->buf[h->cur]);
+    cudaStream_t hs = h->halo_stream;
+    const bool sep = hs != h->stream;
+    // on a separate stream: after the layers an export reads, or the ghost
+    // reads an import overwrites (the last step, or an open step's edges)
+    cudaError_t e = sep ? cudaStreamWaitEvent(hs, h->step_open ? h->ev_edges : h->ev_step, 0) : cudaSuccess;
+    if (e == cudaSuccess && to_other) {
+        // layer z = 0 or nz - 1 of the newest state -> packed [V0 | V1 | V2]
+        const char* b = static_cast<const char*>(h->buf[h->step_open ? h->cur ^ 1 : h->cur]);
         const size_t z = side == 0 ? 0 : (size_t)g.nz - 1, fsb = (size_t)g.fstride * h->elem;
         const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
         char* d = static_cast<char*>(other);
-        e = cudaMemcpyAsync(d, b + z * e4, e4, kind, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d + e4, b + 4 * fsb + z * e4, e4, kind, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d + 2 * e4, b + 8 * fsb + z * e2, e2, kind, h->stream);
-    } else {
+        e = cudaMemcpyAsync(d, b + z * e4, e4, kind, hs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d + e4, b + 4 * fsb + z * e4, e4, kind, hs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d + 2 * e4, b + 8 * fsb + z * e2, e2, kind, hs);
+    } else if (e == cudaSuccess) {
         const cudaMemcpyKind kind = where == TSLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        e = cudaMemcpyAsync(static_cast<char*>(h->ghost) + side * pb, other, pb, kind, h->stream);
+        e = cudaMemcpyAsync(static_cast<char*>(h->ghost) + side * halo_ghost_stride(h), other, pb, kind, hs);
+        if (e == cudaSuccess && sep) e = cudaEventRecord(h->ev_halo, hs);
     }
-    if (e == cudaSuccess && where == TSLB_HOST) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && where == TSLB_HOST) e = cudaStreamSynchronize(hs);
     if (e != cudaSuccess) return cuda_fail(h, e, to_other ? "halo export" : "halo import");
     return TSLB_OK;
 }

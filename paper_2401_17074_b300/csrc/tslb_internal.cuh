@@ -595,11 +595,23 @@ struct tslb_s {
     size_t adj_lam_bytes = 0;
     // halo slab: two packed ghost planes, [side][V0 plane | V1 plane | V2 plane]
     void* ghost = nullptr;
+    // halo slab: the stream of the exports and imports (the handle's own, or
+    // the caller's), and events ordering them against the steps: ev_step after
+    // each completed step, ev_edges after an open step's edges, ev_halo after
+    // the latest import
+    cudaStream_t halo_stream = nullptr;
+    cudaEvent_t ev_step = nullptr, ev_edges = nullptr, ev_halo = nullptr;
+    bool step_open = false;  // between tslb_step_part(EDGES) and (INTERIOR)
     std::string err;
 };
 
 // Bytes of one packed plane of a halo slab: ten stored values per interior node of a layer.
 inline size_t halo_plane_bytes(const tslb_s* h) { return (size_t)NFIELDS_3D * (size_t)h->g.plane * h->elem; }
+// Distance between the two ghost planes in the handle's ghost buffer: the
+// packed plane rounded up to 256 bytes, so that the second plane starts on
+// the alignment the step kernel's 16-byte plane copies need (a packed plane
+// of an odd number of nodes is only 4- or 8-byte aligned at its end).
+inline size_t halo_ghost_stride(const tslb_s* h) { return (halo_plane_bytes(h) + 255) / 256 * 256; }
 
 namespace tslb {
 
@@ -611,6 +623,9 @@ cudaError_t launch_encode2d(const tslb_s* h, const double* rho, const double* u,
 cudaError_t launch_decode2d(const tslb_s* h, const void* src, double* rho, double* u, double* pi);
 cudaError_t launch_diag2d(const tslb_s* h, const void* src, double* out_dev);
 cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p);
+// The factored step over the stored layers [zlo, zhi) only (a split step).
+cudaError_t launch_step_factored_range(const tslb_s* h, const void* src, void* dst, const Physics& p, int zlo,
+                                       int zhi);
 // The step kernel tslb_step uses for this handle (same choice, bitwise-identical results).
 cudaError_t launch_step_any(const tslb_s* h, const void* src, void* dst, const Physics& p);
 bool use_factored(const tslb_s* h);

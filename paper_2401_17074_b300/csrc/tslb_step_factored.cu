@@ -706,7 +706,7 @@ struct Kernel {
 template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE, bool HALO>
 __global__ void __launch_bounds__(NT, 1)
     step_factored_kernel(const typename Codec::T* __restrict__ src, typename Codec::T* __restrict__ dst, Geometry g,
-                         Physics p, int zchunk) {
+                         Physics p, int zlo, int zhi, int zchunk) {
     typedef Kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE, HALO> K;
     // [2][YBUF] y exchange, [2][PF::BUF] plane prefetch, corrections, mbarriers,
     // and with FORCE [2][FBUF] force slots
@@ -773,8 +773,9 @@ __global__ void __launch_bounds__(NT, 1)
         c.offLv = c.offRv = c.offLs = c.offRs = c.tid;
     }
 #endif
-    c.z0 = (int)blockIdx.z * zchunk;
-    c.z1 = min(c.z0 + zchunk, g.nz);
+    // this CTA's z chunk of the launch's layer range [zlo, zhi)
+    c.z0 = zlo + (int)blockIdx.z * zchunk;
+    c.z1 = min(c.z0 + zchunk, zhi);
     c.np = c.z1 - c.z0 + 2;
 
     // Launched with programmatic stream serialisation: the set-up above
@@ -803,8 +804,9 @@ __global__ void __launch_bounds__(NT, 1)
     else K::template march<ROLE_ANY>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
 }
 
+// One step over the layer range [zlo, zhi) of the stored lattice.
 template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE = false, bool HALO = false>
-cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p) {
+cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics& p, int zlo, int zhi) {
     auto kern = step_factored_kernel<Codec, XFREE, SPONGE, NEEY, GUO, FORCE, HALO>;
     static bool configured[64] = {};
     const int dev = h->device;
@@ -822,10 +824,11 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
     // z chunks: fill whole waves of one CTA per SM while keeping chunks long
     // (each chunk re-reads two extra planes).
     const long long tiles = (long long)bx * by;
+    const int nzr = zhi - zlo;
     int best_n = 1;
     double best = 0.0;
-    for (int n = 1; n <= 16 && n <= g.nz; ++n) {
-        const int len = (g.nz + n - 1) / n;
+    for (int n = 1; n <= 16 && n <= nzr; ++n) {
+        const int len = (nzr + n - 1) / n;
         const long long ctas = tiles * n;
         const long long waves = (ctas + sms - 1) / sms;
         const double eff = (double)ctas / (double)(waves * sms) * (double)len / (double)(len + 2);
@@ -834,8 +837,8 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
             best_n = n;
         }
     }
-    const int zchunk = (g.nz + best_n - 1) / best_n;
-    const unsigned bz = (unsigned)((g.nz + zchunk - 1) / zchunk);
+    const int zchunk = (nzr + best_n - 1) / best_n;
+    const unsigned bz = (unsigned)((nzr + zchunk - 1) / zchunk);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(bx, by, bz);
     cfg.blockDim = dim3(NT);
@@ -846,28 +849,29 @@ cudaError_t launch_t(const tslb_s* h, const void* src, void* dst, const Physics&
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, (const typename Codec::T*)src, (typename Codec::T*)dst, g, p, zchunk);
+    return cudaLaunchKernelEx(&cfg, kern, (const typename Codec::T*)src, (typename Codec::T*)dst, g, p, zlo, zhi,
+                              zchunk);
 }
 
 template <class Codec>
-cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Physics& p) {
+cudaError_t launch_codec(const tslb_s* h, const void* src, void* dst, const Physics& p, int zlo, int zhi) {
     const bool xfree = h->g.bc[0] == TSLB_BC_FREESLIP, sponge = p.omega1_z != nullptr;
     // halo slabs: periodic x, periodic or bounce-back y, Luo forcing, constant
     // force (checked at create)
-    if (h->g.bc[4] == TSLB_BC_HALO) return launch_t<Codec, false, false, false, false, false, true>(h, src, dst, p);
+    if (h->g.bc[4] == TSLB_BC_HALO) return launch_t<Codec, false, false, false, false, false, true>(h, src, dst, p, zlo, zhi);
     // Guo forcing comes with periodic x, no sponge and no NEE walls; NEE y walls
     // with periodic x (both checked at create)
-    if (p.guo) return launch_t<Codec, false, false, false, true>(h, src, dst, p);
+    if (p.guo) return launch_t<Codec, false, false, false, true>(h, src, dst, p, zlo, zhi);
     if (h->g.bc[2] == TSLB_BC_NEE_WALL)
-        return sponge ? launch_t<Codec, false, true, true, false>(h, src, dst, p)
-                      : launch_t<Codec, false, false, true, false>(h, src, dst, p);
+        return sponge ? launch_t<Codec, false, true, true, false>(h, src, dst, p, zlo, zhi)
+                      : launch_t<Codec, false, false, true, false>(h, src, dst, p, zlo, zhi);
     if (xfree)
-        return sponge ? launch_t<Codec, true, true, false, false>(h, src, dst, p)
-                      : launch_t<Codec, true, false, false, false>(h, src, dst, p);
-    if (sponge) return launch_t<Codec, false, true, false, false>(h, src, dst, p);
+        return sponge ? launch_t<Codec, true, true, false, false>(h, src, dst, p, zlo, zhi)
+                      : launch_t<Codec, true, false, false, false>(h, src, dst, p, zlo, zhi);
+    if (sponge) return launch_t<Codec, false, true, false, false>(h, src, dst, p, zlo, zhi);
     // a force field: its components prefetched with the moments
-    return p.force ? launch_t<Codec, false, false, false, false, true>(h, src, dst, p)
-                   : launch_t<Codec, false, false, false, false>(h, src, dst, p);
+    return p.force ? launch_t<Codec, false, false, false, false, true>(h, src, dst, p, zlo, zhi)
+                   : launch_t<Codec, false, false, false, false>(h, src, dst, p, zlo, zhi);
 }
 
 }  // namespace
@@ -880,16 +884,22 @@ bool factored_supports(const tslb_s* h) {
     return (long long)h->g.plane * h->g.nz < (1LL << 32);
 }
 
-cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p) {
+cudaError_t launch_step_factored_range(const tslb_s* h, const void* src, void* dst, const Physics& p, int zlo,
+                                       int zhi) {
+    if (zhi <= zlo) return cudaSuccess;
     switch (h->precision) {
-        case TSLB_FP32: return launch_codec<CodecF32>(h, src, dst, p);
+        case TSLB_FP32: return launch_codec<CodecF32>(h, src, dst, p, zlo, zhi);
         case TSLB_BF16:
-            return h->rounding == TSLB_ROUND_STOCHASTIC ? launch_codec<CodecBF16SR>(h, src, dst, p)
-                                                        : launch_codec<CodecBF16>(h, src, dst, p);
+            return h->rounding == TSLB_ROUND_STOCHASTIC ? launch_codec<CodecBF16SR>(h, src, dst, p, zlo, zhi)
+                                                        : launch_codec<CodecBF16>(h, src, dst, p, zlo, zhi);
         default:
-            return h->rounding == TSLB_ROUND_STOCHASTIC ? launch_codec<CodecF16SR>(h, src, dst, p)
-                                                        : launch_codec<CodecF16>(h, src, dst, p);
+            return h->rounding == TSLB_ROUND_STOCHASTIC ? launch_codec<CodecF16SR>(h, src, dst, p, zlo, zhi)
+                                                        : launch_codec<CodecF16>(h, src, dst, p, zlo, zhi);
     }
+}
+
+cudaError_t launch_step_factored(const tslb_s* h, const void* src, void* dst, const Physics& p) {
+    return launch_step_factored_range(h, src, dst, p, 0, h->g.nz);
 }
 
 }  // namespace tslb

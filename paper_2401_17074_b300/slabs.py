@@ -12,7 +12,10 @@ Two drivers share the same exchange pattern:
 * ``SlabChain`` keeps every slab in this process, on one device and one
   stream, and moves the packed planes with device copies.  Stream order makes
   the sequence export -> import -> step correct without further
-  synchronisation.
+  synchronisation.  With ``overlap=True`` every step is split
+  (tslb_step_part): the slabs' edge layers first, then their interiors on the
+  compute stream while the exports and imports run on a second stream, which
+  the library orders against the steps with events.
 * ``exchange_halos`` is the multi-process form: one slab per rank, the packed
   planes sent to and received from the ring neighbours with
   ``torch.distributed`` point-to-point operations (NCCL for CUDA buffers, gloo
@@ -21,7 +24,7 @@ Two drivers share the same exchange pattern:
 """
 import numpy as np
 
-from . import FP32, HALO, PERIODIC, Solver
+from . import FP32, HALO, PERIODIC, TSLB_PART_EDGES, TSLB_PART_INTERIOR, Solver
 
 # message tags: planes travelling up the ring (a slab's top layer to the next
 # slab's lower ghost) and down it (bottom layer to the previous slab's upper ghost)
@@ -73,6 +76,25 @@ def exchange_halos(slab, bufs, dist):
     slab.halo_import(1, recv_hi)
 
 
+def step_overlapped(slab, bufs, dist, halo_stream):
+    """One step of this rank's slab with its halo exchange overlapping the
+    update of the slab's interior layers.
+
+    slab: a Solver with halo faces created with halo_stream=halo_stream.cuda_stream
+    (a torch.cuda.Stream).  The edge layers are advanced first; the exchange
+    then runs on halo_stream (exports wait for the edges, the point-to-point
+    operations are queued behind them on the same stream, imports behind
+    those) while the interior layers are advanced on the slab's own stream;
+    the next step waits for the imports.  The ghosts of the initial state
+    must be in place before the first such step: call exchange_halos once
+    after init_moments."""
+    import torch
+    slab.step_part(TSLB_PART_EDGES)
+    with torch.cuda.stream(halo_stream):
+        exchange_halos(slab, bufs, dist)
+    slab.step_part(TSLB_PART_INTERIOR)
+
+
 def _zslice(a, dims, z0, z1, ncomp):
     """Layers z0 .. z1-1 of a full-lattice array with ncomp components."""
     nx, ny, nz = dims
@@ -91,16 +113,20 @@ class SlabChain:
     """
 
     def __init__(self, dims, tau, nslabs, force=(0.0, 0.0, 0.0), bc=(0,) * 6, precision=FP32, u_ref=0.05,
-                 pi_ref=1e-3, device=0):
+                 pi_ref=1e-3, device=0, overlap=False):
         import torch
         if bc[4] != PERIODIC or bc[5] != PERIODIC:
             raise ValueError("a slab chain is periodic in z")
         self.dims = tuple(int(d) for d in dims)
         self.ranges = split(self.dims[2], nslabs)
         self.stream = torch.cuda.Stream(device=device)
+        self.overlap = bool(overlap)
+        self.halo_stream = torch.cuda.Stream(device=device) if self.overlap else None
+        hs = self.halo_stream.cuda_stream if self.overlap else None
         sbc = tuple(bc[:4]) + (HALO, HALO)
         self.slabs = [Solver((self.dims[0], self.dims[1], z1 - z0), tau, force=force, bc=sbc, precision=precision,
-                             u_ref=u_ref, pi_ref=pi_ref, device=device, stream=self.stream.cuda_stream)
+                             u_ref=u_ref, pi_ref=pi_ref, device=device, stream=self.stream.cuda_stream,
+                             halo_stream=hs)
                       for z0, z1 in self.ranges]
         nb = self.slabs[0].halo_plane_bytes()
         self.bufs = [[torch.empty(nb, dtype=torch.uint8, device="cuda:%d" % device) for _ in range(2)]
@@ -114,6 +140,10 @@ class SlabChain:
         for s, (z0, z1) in zip(self.slabs, self.ranges):
             s.init_moments(_zslice(rho, self.dims, z0, z1, 1).reshape(-1), _zslice(u, self.dims, z0, z1, 3),
                            None if pi is None else _zslice(pi, self.dims, z0, z1, 6))
+        if self.overlap:
+            # an overlapped step exchanges the layers of the state it produces,
+            # so the ghosts of the initial state are filled here
+            self.exchange()
 
     def exchange(self):
         n = len(self.slabs)
@@ -126,9 +156,18 @@ class SlabChain:
 
     def step(self, n=1):
         for _ in range(int(n)):
-            self.exchange()
-            for slab in self.slabs:
-                slab.step(1)
+            if self.overlap:
+                # the edges need the ghosts of this step's state; the exchange of
+                # the new edge layers then overlaps the interiors
+                for slab in self.slabs:
+                    slab.step_part(TSLB_PART_EDGES)
+                self.exchange()
+                for slab in self.slabs:
+                    slab.step_part(TSLB_PART_INTERIOR)
+            else:
+                self.exchange()
+                for slab in self.slabs:
+                    slab.step(1)
 
     def get_moments(self):
         nx, ny, nz = self.dims

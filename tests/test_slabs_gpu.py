@@ -25,14 +25,19 @@ def _single(dims, tau, force, bc, state, nsteps, **kw):
     return out
 
 
-@pytest.mark.parametrize("case", ["channel-2", "channel-3-ragged", "periodic-4", "bf16-channel-2"])
-def test_slab_chain_matches_single_domain(cuda_ok, case):
+@pytest.mark.parametrize("overlap", [False, True], ids=["sequential", "overlapped"])
+@pytest.mark.parametrize("case", ["channel-2", "channel-3-ragged", "periodic-4", "periodic-odd-3", "bf16-channel-2",
+                                  "bf16-odd-2"])
+def test_slab_chain_matches_single_domain(cuda_ok, case, overlap):
+    # "odd": layers of an odd number of nodes (33 x 21 and 33 x 15), whose packed
+    # planes end off the 16-byte boundary the second ghost plane must start on
     if case.startswith("channel") or case.startswith("bf16"):
-        prm = W.channel_params(nx=40, ny=18, nz=26 if "ragged" in case else 24)
+        prm = W.channel_params(nx=33 if "odd" in case else 40, ny=17 if "odd" in case else 18,
+                               nz=26 if "ragged" in case else 24)
         dims, tau, force, bc = prm["dims"], prm["tau"], prm["force"], prm["bc"]
         state = W.channel_state(prm, seed=1)
     else:
-        dims, tau, force, bc = (34, 21, 29), 0.62, (2e-6, -1e-6, 3e-6), (0,) * 6
+        dims, tau, force, bc = ((33, 21, 29) if "odd" in case else (34, 21, 29)), 0.62, (2e-6, -1e-6, 3e-6), (0,) * 6
         state = W.random_state(dims, seed=81)
     nslabs = int(case.split("-")[-1]) if case.split("-")[-1].isdigit() else int(case.split("-")[-2])
     kw = {}
@@ -40,7 +45,7 @@ def test_slab_chain_matches_single_domain(cuda_ok, case):
         kw = dict(precision=T.BF16, u_ref=0.05, pi_ref=W.pi_reference(state))
     nsteps = 15
     ref = _single(dims, tau, force, bc, state, nsteps, **kw)
-    chain = SlabChain(dims, tau, nslabs, force=force, bc=bc, **kw)
+    chain = SlabChain(dims, tau, nslabs, force=force, bc=bc, overlap=overlap, **kw)
     chain.init_moments(*state)
     chain.step(nsteps)
     got = chain.get_moments()
@@ -63,6 +68,7 @@ def test_halo_plane_round_trip(cuda_ok):
     s.halo_export(1, host)
     dev = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     s.halo_export(1, dev)
+    s.synchronize()  # the export ran on the handle's stream
     assert np.array_equal(host, dev.cpu().numpy())
     v0 = host[: 4 * 4 * 84].view(np.float32).reshape(84, 4)  # (u_x, u_y, u_z, rho - 1) of layer z = 5
     rho, u, _ = s.get_moments()
@@ -96,10 +102,10 @@ def test_slab_chain_random_cases(cuda_ok):
     from hypothesis import given, settings, HealthCheck, strategies as st
 
     @settings(max_examples=25, deadline=None, suppress_health_check=list(HealthCheck))
-    @given(nx=st.integers(3, 45), ny=st.integers(4, 36), nslabs=st.integers(2, 5), extra=st.integers(0, 7),
+    @given(nx=st.integers(3, 45), ny=st.integers(4, 36), nslabs=st.integers(2, 5), extra=st.integers(0, 30),
            walls=st.booleans(), prec=st.sampled_from([T.FP32, T.BF16, T.FP16]), tau=st.floats(0.51, 1.5),
-           steps=st.integers(1, 9), seed=st.integers(0, 10 ** 6))
-    def run(nx, ny, nslabs, extra, walls, prec, tau, steps, seed):
+           steps=st.integers(1, 9), seed=st.integers(0, 10 ** 6), overlap=st.booleans())
+    def run(nx, ny, nslabs, extra, walls, prec, tau, steps, seed, overlap):
         nz = 3 * nslabs + extra
         dims = (nx, ny, nz)
         bc = (0, 0, 1, 1, 0, 0) if walls else (0,) * 6
@@ -107,7 +113,7 @@ def test_slab_chain_random_cases(cuda_ok):
         force = (1e-5, -2e-6, 3e-6)
         kw = {} if prec == T.FP32 else dict(precision=prec, u_ref=0.05, pi_ref=W.pi_reference(state))
         ref = _single(dims, tau, force, bc, state, steps, **kw)
-        chain = SlabChain(dims, tau, nslabs, force=force, bc=bc, **kw)
+        chain = SlabChain(dims, tau, nslabs, force=force, bc=bc, overlap=overlap, **kw)
         chain.init_moments(*state)
         chain.step(steps)
         got = chain.get_moments()
@@ -116,3 +122,36 @@ def test_slab_chain_random_cases(cuda_ok):
             assert np.array_equal(a, b)
 
     run()
+
+
+def test_split_step_states(cuda_ok):
+    """tslb_step_part keeps a simple state machine: EDGES then INTERIOR; a
+    whole step, an initialisation or a second EDGES while a split step is
+    open, and INTERIOR with none open, are refused; a handle without halo
+    faces has no split steps.  EDGES + INTERIOR equals tslb_step bit for bit
+    (slab of 20 layers, so the edge and interior launches are both used)."""
+    dims = (14, 9, 20)
+    state = W.random_state(dims, seed=83)
+    a = T.Solver(dims, 0.7, bc=(0, 0, 0, 0, T.HALO, T.HALO))
+    b = T.Solver(dims, 0.7, bc=(0, 0, 0, 0, T.HALO, T.HALO))
+    for s in (a, b):
+        s.init_moments(*state)
+    with pytest.raises(T.TslbError) as ei:
+        a.step_part(T.TSLB_PART_INTERIOR)
+    assert ei.value.code == T.TSLB_ERR_STATE
+    a.step_part(T.TSLB_PART_EDGES)
+    for bad in (lambda: a.step_part(T.TSLB_PART_EDGES), lambda: a.step(1), lambda: a.init_moments(*state)):
+        with pytest.raises(T.TslbError) as ei:
+            bad()
+        assert ei.value.code == T.TSLB_ERR_STATE
+    a.step_part(T.TSLB_PART_INTERIOR)
+    b.step(1)
+    for x, y in zip(a.get_moments(), b.get_moments()):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+    c = T.Solver(dims, 0.7)
+    with pytest.raises(T.TslbError) as ei:
+        c.step_part(T.TSLB_PART_EDGES)
+    assert ei.value.code == T.TSLB_ERR_STATE
+    c.close()
