@@ -217,6 +217,7 @@ def test_paper_jet_full_size_sampled(cuda_ok):
     _check(pairs, 3e-6)
 
 
+@pytest.mark.gpu
 def test_bf16_lattice_beyond_2_31_nodes(cuda_ok):
     """A BF16 lattice of 1024 x 1024 x 2049 = 2,148,532,224 nodes (more than
     2^31; 86 GB for the two moment buffers) runs the factored kernel, and three
