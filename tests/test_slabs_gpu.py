@@ -155,3 +155,29 @@ def test_split_step_states(cuda_ok):
         c.step_part(T.TSLB_PART_EDGES)
     assert ei.value.code == T.TSLB_ERR_STATE
     c.close()
+
+
+def test_step_overlapped_single_rank_ring(cuda_ok):
+    """The multi-process step (slabs.step_overlapped with exchange_halos) on one
+    rank: the slab is its own neighbour on both sides, the exchange runs on a
+    second stream through CUDA buffers, and a lattice periodic in z as one
+    halo slab must equal a plain periodic handle bit for bit."""
+    import torch
+    from paper_2401_17074_b300.slabs import exchange_halos, step_overlapped
+    dims, tau = (37, 19, 23), 0.66
+    state = W.random_state(dims, seed=84)
+    force = (3e-6, 1e-6, -2e-6)
+    ref = _single(dims, tau, force, (0,) * 6, state, 11)
+    hs = torch.cuda.Stream()
+    s = T.Solver(dims, tau, force=force, bc=(0, 0, 0, 0, T.HALO, T.HALO), halo_stream=hs.cuda_stream)
+    s.init_moments(*state)
+    nb = s.halo_plane_bytes()
+    bufs = tuple(torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(4))
+    with torch.cuda.stream(hs):
+        exchange_halos(s, bufs, None)  # the ghosts of the initial state
+    for _ in range(11):
+        step_overlapped(s, bufs, None, hs)
+    got = s.get_moments()
+    s.close()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
