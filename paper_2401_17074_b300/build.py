@@ -30,7 +30,9 @@ SOURCES = [
     "tslb_step_factored.cu",
     "tslb_step_factored_f32.cu",
     "tslb_step_factored_bf16.cu",
+    "tslb_step_factored_bf16sr.cu",
     "tslb_step_factored_f16.cu",
+    "tslb_step_factored_f16sr.cu",
     "tslb_adjoint.cu",
     "tslb_noalloc.cu",
     "tslb_step2d.cu",

@@ -1,5 +1,5 @@
 // Dispatch of the sum-factorised step to the per-storage-type instances
-// (tslb_step_factored_f32.cu, _bf16.cu, _f16.cu; kernels in tslb_step_factored.cuh).
+// (tslb_step_factored_{f32,bf16,bf16sr,f16,f16sr}.cu; kernels in tslb_step_factored.cuh).
 #include "tslb_internal.cuh"
 
 namespace tslb {

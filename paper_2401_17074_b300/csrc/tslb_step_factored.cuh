@@ -47,8 +47,7 @@
 // outflow, Sec. 3.2).
 #pragma once
 // (The kernel templates of the sum-factorised step; each storage type is
-// instantiated in a translation unit of its own, tslb_step_factored_<type>.cu,
-// so the heavy compiles run in parallel.)
+// instantiated in a translation unit of its own, tslb_step_factored_<type>.cu.)
 #include <algorithm>
 
 #include "tslb_internal.cuh"
