@@ -400,12 +400,15 @@ def precision_study(T, torch, stream, prm, state, warm=1000, window=5000, every=
     for run in ("bf16", "fp16", "bf16_sr", "fp16_sr"):
         out[run + "_vs_fp32"] = profile_errors(runs[run][0], ref)
     out["note"] = ("_sr: stochastic rounding of the stored rho - 1 and u; without it the per-step body-force "
-                   "increment (%.3g) is below half a 16-bit spacing of u and is lost" % prm["force"][0])
+                   "increment (%.3g) is below half a 16-bit spacing of u and is lost.  From the laminar start the "
+                   "flow is still laminar in this window: the fluctuations are the decaying seeded noise (stress "
+                   "scales in fp32_scale), so the stress errors compare noise, and U carries the result.  The "
+                   "study on developed turbulence is bench.py --only precision-study" % prm["force"][0])
     return out
 
 
 def turbulent_precision_study(T, torch, warm=300000, window=100000, every=1000, check=10000):
-    """Config 4 on developed turbulence: the full channel from a disturbed state
+    """The 16-bit storage study on developed turbulence: the full channel from a disturbed state
     (workloads.channel_transition_state) run in FP32 for `warm` steps, its
     bulk velocity, wall shear and maximum speed recorded every `check` steps;
     then, from that state, runs of `window` steps in FP32, in FP32 from the
