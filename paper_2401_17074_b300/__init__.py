@@ -397,6 +397,9 @@ class Solver:
             o.sponge_k = float(sponge[1])
         self.dims = tuple(int(d) for d in dims)
         self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        # the stream the halo copies run on, where the caller chose it (None: the
+        # handle's own stream, which PyTorch cannot see)
+        self.halo_copy_stream = halo_stream if halo_stream is not None else stream
         self._h = tslb_create(self.dims, tau, force, bc, o, lattice=TSLB_D3Q27 if lattice is None else lattice)
 
     @property

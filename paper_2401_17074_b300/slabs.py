@@ -22,6 +22,8 @@ Two drivers share the same exchange pattern:
   for CPU buffers).  A slab is any object with ``halo_export(side, buf)`` and
   ``halo_import(side, buf)``, so the bookkeeping can run on CPU stand-ins.
 """
+import contextlib
+
 import numpy as np
 
 from . import FP32, HALO, PERIODIC, TSLB_PART_EDGES, TSLB_PART_INTERIOR, Solver
@@ -56,7 +58,16 @@ def exchange_halos(slab, bufs, dist):
     each (CUDA tensors with NCCL, CPU tensors with gloo).  The slab's bottom
     layer goes down the ring and its top layer up; the planes received fill
     its ghost layers below (from the rank below) and above (from the rank
-    above).  With one rank the slab is its own neighbour on both sides."""
+    above).  With one rank the slab is its own neighbour on both sides.
+
+    With CUDA buffers the exports and imports run on the slab's halo-copy
+    stream and the point-to-point operations on PyTorch's current stream, so
+    the two are ordered here: where the slab's stream is known
+    (slab.halo_copy_stream, the stream or halo_stream the Solver was created
+    with) the operations are issued with that stream current, so they follow
+    the exports and the imports follow their completion without a host wait;
+    otherwise (the handle's own stream) the host waits for the exports before
+    the sends and for the receives before the imports."""
     send_lo, send_hi, recv_lo, recv_hi = bufs
     slab.halo_export(0, send_lo)
     slab.halo_export(1, send_hi)
@@ -66,14 +77,25 @@ def exchange_halos(slab, bufs, dist):
         slab.halo_import(1, send_lo)
         return
     lo, hi = ring_neighbours(dist.get_rank(), world)
-    ops = [dist.P2POp(dist.isend, send_hi, hi, tag=TAG_UP),
-           dist.P2POp(dist.irecv, recv_lo, lo, tag=TAG_UP),
-           dist.P2POp(dist.isend, send_lo, lo, tag=TAG_DOWN),
-           dist.P2POp(dist.irecv, recv_hi, hi, tag=TAG_DOWN)]
-    for r in dist.batch_isend_irecv(ops):
-        r.wait()
-    slab.halo_import(0, recv_lo)
-    slab.halo_import(1, recv_hi)
+    cuda = bool(getattr(send_lo, "is_cuda", False))
+    ctx, sp = contextlib.nullcontext(), getattr(slab, "halo_copy_stream", None)
+    if cuda:
+        import torch
+        if sp is not None:
+            ctx = torch.cuda.stream(torch.cuda.ExternalStream(int(sp), device=send_lo.device))
+        else:
+            slab.synchronize()
+    with ctx:
+        ops = [dist.P2POp(dist.isend, send_hi, hi, tag=TAG_UP),
+               dist.P2POp(dist.irecv, recv_lo, lo, tag=TAG_UP),
+               dist.P2POp(dist.isend, send_lo, lo, tag=TAG_DOWN),
+               dist.P2POp(dist.irecv, recv_hi, hi, tag=TAG_DOWN)]
+        for r in dist.batch_isend_irecv(ops):
+            r.wait()
+        if cuda and sp is None:
+            torch.cuda.current_stream(send_lo.device).synchronize()
+        slab.halo_import(0, recv_lo)
+        slab.halo_import(1, recv_hi)
 
 
 def step_overlapped(slab, bufs, dist, halo_stream):

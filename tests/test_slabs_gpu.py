@@ -181,3 +181,94 @@ def test_step_overlapped_single_rank_ring(cuda_ok):
     s.close()
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
+
+
+class _LoopbackDist:
+    """A stand-in for torch.distributed with the NCCL stream semantics, on one
+    GPU: world size 2 with every message coming back to this rank by its tag
+    (the slab is its own ring neighbour on both sides).  A batch runs on a
+    communication stream of its own that waits for the current stream when
+    the batch is issued, sleeps for about a millisecond (so that an exchange
+    ordered against the wrong stream reads or leaves stale planes) and then
+    copies; a work's wait() makes the current stream wait for the batch."""
+
+    isend, irecv = "send", "recv"
+
+    class P2POp:
+        def __init__(self, op, tensor, peer, tag=0):
+            self.op, self.tensor, self.peer, self.tag = op, tensor, peer, tag
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.comm = torch.cuda.Stream()
+
+    def get_world_size(self):
+        return 2
+
+    def get_rank(self):
+        return 0
+
+    def batch_isend_irecv(self, ops):
+        torch = self.torch
+        self.comm.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.comm):
+            torch.cuda._sleep(2_000_000)
+            sent = {o.tag: o.tensor for o in ops if o.op == self.isend}
+            for o in ops:
+                if o.op == self.irecv:
+                    o.tensor.copy_(sent[o.tag])
+        done = torch.cuda.Event()
+        done.record(self.comm)
+
+        class Work:
+            def wait(self_):
+                torch.cuda.current_stream().wait_event(done)
+
+        return [Work() for _ in ops]
+
+
+@pytest.mark.parametrize("mode", ["handle-stream", "caller-stream", "overlapped"])
+def test_exchange_halos_stream_order(cuda_ok, mode):
+    """exchange_halos with CUDA buffers and point-to-point operations on
+    another stream (the NCCL semantics, emulated on one GPU): the exports must
+    complete before the sends read the buffers and the receives before the
+    imports, whether the slab runs on the handle's own stream (host waits),
+    on a stream the caller gave (stream order), or with the exchange on a
+    halo stream overlapping the interior update.  A lattice periodic in z as
+    one halo slab must equal a plain periodic handle bit for bit."""
+    import torch
+    from paper_2401_17074_b300.slabs import exchange_halos, step_overlapped
+    dims, tau, nsteps = (41, 17, 19), 0.71, 9
+    state = W.random_state(dims, seed=85)
+    force = (2e-6, -1e-6, 1e-6)
+    ref = _single(dims, tau, force, (0,) * 6, state, nsteps)
+    dist = _LoopbackDist()
+    bc = (0, 0, 0, 0, T.HALO, T.HALO)
+    st = torch.cuda.Stream()
+    if mode == "handle-stream":
+        s = T.Solver(dims, tau, force=force, bc=bc)
+    elif mode == "caller-stream":
+        s = T.Solver(dims, tau, force=force, bc=bc, stream=st.cuda_stream)
+    else:
+        s = T.Solver(dims, tau, force=force, bc=bc, halo_stream=st.cuda_stream)
+    s.init_moments(*state)
+    nb = s.halo_plane_bytes()
+    bufs = tuple(torch.zeros(nb, dtype=torch.uint8, device="cuda") for _ in range(4))
+    if mode == "overlapped":
+        with torch.cuda.stream(st):
+            exchange_halos(s, bufs, dist)
+        for _ in range(nsteps):
+            step_overlapped(s, bufs, dist, st)
+    else:
+        for _ in range(nsteps):
+            if mode == "caller-stream":
+                # a late export: the sends must wait for it on the slab's stream
+                with torch.cuda.stream(st):
+                    torch.cuda._sleep(1_000_000)
+            exchange_halos(s, bufs, dist)
+            s.step(1)
+    got = s.get_moments()
+    s.close()
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
