@@ -374,6 +374,9 @@ template <class Codec, bool XFREE, bool SPONGE, bool NEEY, bool GUO, bool FORCE,
 struct Kernel {
     typedef typename Codec::T T;
     static constexpr bool HOIST = sizeof(T) != 4;
+    // the variants launched only without a force field (the plain one is
+    // replaced by FORCE when there is one; halo slabs reject it at create)
+    static constexpr bool NOFIELD = !FORCE && ((!XFREE && !SPONGE && !NEEY && !GUO) || HALO);
 
     // One march position j (plane zs = z0 - 1 + j).  ppOld holds p+ of plane
     // zs-2 on entry and p+ of plane zs on exit; cOld holds c of zs-1; cNew
@@ -419,6 +422,14 @@ struct Kernel {
             F0 = f[0];
             F1 = f[1];
             F2 = f[2];
+        } else if (NOFIELD) {
+#ifdef TSLB_CHECKED
+            // a force field handed to a variant that never reads one
+            if (p.force && p.err) atomicOr(p.err, TSLB_ERR_BIT_INDEX);
+#endif
+            F0 = p.F[0];
+            F1 = p.F[1];
+            F2 = p.F[2];
         } else {
             load_force(p, g, idx, F0, F1, F2);
         }
