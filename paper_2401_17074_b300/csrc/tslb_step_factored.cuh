@@ -544,12 +544,20 @@ struct Kernel {
                 f2 LA[3], RA[3];
                 float Ls[3], Rs[3];
                 {
-                    const float4 l0 = sv[0 * NT + c.offLv], l1 = sv[1 * NT + c.offLv];
-                    const float4 r0 = sv[2 * NT + c.offRv], r1 = sv[3 * NT + c.offRv];
+                    // plain and wall rows of the variants with periodic x read
+                    // the rows below and above (their offsets are constants);
+                    // the others may read their own slots on a free-slip wall row
+                    constexpr bool COFF = ROLE != ROLE_ANY && !XFREE;
+                    const int offLv = COFF ? c.tid - 32 : c.offLv;
+                    const int offRv = COFF ? c.tid + 32 : c.offRv;
+                    const int offLs = COFF ? c.tid - 32 : c.offLs;
+                    const int offRs = COFF ? c.tid + 32 : c.offRs;
+                    const float4 l0 = sv[0 * NT + offLv], l1 = sv[1 * NT + offLv];
+                    const float4 r0 = sv[2 * NT + offRv], r1 = sv[3 * NT + offRv];
                     LA[0] = make_float2(l0.x, l0.y); LA[1] = make_float2(l0.z, l0.w); LA[2] = make_float2(l1.x, l1.y);
                     RA[0] = make_float2(r0.x, r0.y); RA[1] = make_float2(r0.z, r0.w); RA[2] = make_float2(r1.x, r1.y);
-                    Ls[0] = l1.z; Ls[1] = l1.w; Ls[2] = ss[c.offLs];
-                    Rs[0] = r1.z; Rs[1] = r1.w; Rs[2] = ss[NT + c.offRs];
+                    Ls[0] = l1.z; Ls[1] = l1.w; Ls[2] = ss[offLs];
+                    Rs[0] = r1.z; Rs[1] = r1.w; Rs[2] = ss[NT + offRs];
                 }
                 // y moments in x-pass pair layout: Y03 = (q,r) groups (0,0) and (0,1),
                 // Y14 = (1,0) and (1,1), Y25 = (2,0) and (0,2)
@@ -805,7 +813,7 @@ __global__ void __launch_bounds__(NT, 1)
     // with only the wall correction; the halo, ghost and NEE rows run the
     // general one.
     const bool plain = uni(c.warp >= 1 && c.warp <= YOUT && c.out_row && !c.zero_row && !c.nee_row &&
-                           !(c.ybb && (c.row_lo || c.row_hi)));
+                           !((c.ybb || (!XFREE && yfs)) && (c.row_lo || c.row_hi)));
     // (the wall march exists only in the 16-bit variants that can have
     // bounce-back walls -- periodic x, no NEE walls, no sponge: BF16 channel
     // 66.5 -> 68.1 GLUPS; with FP32 storage the third march made the kernel
