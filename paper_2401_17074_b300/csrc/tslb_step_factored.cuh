@@ -375,7 +375,7 @@ struct Kernel {
     typedef typename Codec::T T;
     static constexpr bool HOIST = sizeof(T) != 4;
     // the variants launched only without a force field (the plain one is
-    // replaced by FORCE when there is one; halo slabs reject it at create)
+    // replaced by FORCE when there is one; halo slabs refuse one in tslb_set_force_field)
     static constexpr bool NOFIELD = !FORCE && ((!XFREE && !SPONGE && !NEEY && !GUO) || HALO);
 
     // One march position j (plane zs = z0 - 1 + j).  ppOld holds p+ of plane
