@@ -16,9 +16,9 @@
 //     M0 = p+(x-1) + p0(x) + p-(x+1),  M1 = p+(x-1) - p-(x+1),  M2 = p+(x-1) + p-(x+1).
 // Order of the passes: z in registers (each thread owns an (x, y) column and
 // marches z, so z-neighbours are the previous / next loop iterations), then y
-// through shared memory (warps are rows), then x through warp shuffles
-// (lanes are columns).  Halo: lanes 0 and 31 and the first and last warp
-// recompute the border columns / rows of the tile; the halo warps stop after
+// through shared memory (each warp is a row), then x through warp shuffles
+// (lanes are columns).  Halo: lanes 0 and 31 and the first and last row
+// recompute the border columns / rows of the tile; the halo rows stop after
 // feeding the y exchange.  The z pass starts from the unscaled Hermite
 // coefficients with the mode scale factors folded into its fused
 // multiply-adds.  The regular stages run on packed FP32x2 instructions over
@@ -741,9 +741,21 @@ __global__ void __launch_bounds__(NT, 1)
     bool dead = false;
 
     Ctx c;
-    c.tid = threadIdx.x;
-    c.lane = c.tid & 31;
-    c.warp = c.tid >> 5;
+    // Rows to warps.  Warp w issues on SMSP w % 4, so two of the four SMSPs
+    // hold five of the 18 warps.  The halo rows 0 and 17 (the lightest:
+    // they stop after the y exchange) take warps 0 and 1 on those two, and the
+    // rows next to them (the wall rows of a tile at a y wall, the heaviest
+    // there) warps 2 and 3 on the SMSPs with four; rows 2 .. 15 take warps
+    // 4 .. 17.  Everything below is the row's: c.warp is the row and
+    // c.tid = 32 c.warp + lane its slot index.  (Tiles at a bounce-back wall
+    // had paced the launch: 3.6 % (FP32) and 5.9 % (BF16) longer than the
+    // others with rows on their own warps.)
+    {
+        const int hw = (int)(threadIdx.x >> 5);
+        c.lane = (int)(threadIdx.x & 31);
+        c.warp = hw == 0 ? 0 : hw == 1 ? WROWS - 1 : hw == 2 ? 1 : hw == 3 ? WROWS - 2 : hw - 2;
+        c.tid = c.warp * 32 + c.lane;
+    }
     const int x0 = (int)blockIdx.x * XOUT, y0 = (int)blockIdx.y * YOUT;
     c.x = x0 + c.lane - 1;
     c.y = y0 + c.warp - 1;
