@@ -352,7 +352,7 @@ template <bool HOIST>
 __device__ __forceinline__ bool role(bool v) { return HOIST ? v : uni(v); }
 
 // March specialisations by warp role (see Kernel::march).
-constexpr int ROLE_ANY = 0, ROLE_PLAIN = 1, ROLE_WALL = 2;
+constexpr int ROLE_ANY = 0, ROLE_PLAIN = 1;
 
 // Per-thread constants of the march.
 struct Ctx {
@@ -438,9 +438,7 @@ struct Kernel {
     // STEADY: 2 <= j <= np - 3, so the plane and the next one are stored
     // interior planes inside the chunk (no wrap, no ghost, exchange active).
     // ROLE: ROLE_PLAIN for an output row with no wall, ghost or NEE role (its
-    // role tests are compile-time constants), ROLE_WALL for an output row next
-    // to a bounce-back wall and nothing else (only the wall correction is
-    // tested, per side), ROLE_ANY for the others (tests
+    // role tests are compile-time constants), ROLE_ANY for the others (tests
     // at run time on the warp's role flags).
     template <int PAR, bool STEADY, int ROLE>
     static __device__ __forceinline__ void plane_step(const Ctx& c, const Geometry& g, const Physics& p,
@@ -544,9 +542,9 @@ struct Kernel {
                 f2 LA[3], RA[3];
                 float Ls[3], Rs[3];
                 {
-                    // plain and wall rows of the variants with periodic x read
-                    // the rows below and above (their offsets are constants);
-                    // the others may read their own slots on a free-slip wall row
+                    // plain rows of the variants with periodic x read the rows
+                    // below and above (their offsets are constants); the others
+                    // may read their own slots on a free-slip wall row
                     constexpr bool COFF = ROLE != ROLE_ANY && !XFREE;
                     const int offLv = COFF ? c.tid - 32 : c.offLv;
                     const int offRv = COFF ? c.tid + 32 : c.offRv;
@@ -598,7 +596,7 @@ struct Kernel {
                 // ---- halfway bounce-back on the wall-adjacent rows ----------
                 // The ghost row next to the wall computed the correction for
                 // this plane one march step earlier (see bounce_back_correction).
-                if (ROLE == ROLE_WALL || (ROLE == ROLE_ANY && c.ybb)) {
+                if (ROLE == ROLE_ANY && c.ybb) {
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
                         if (!role<HOIST>(side == 0 ? c.row_lo : c.row_hi)) continue;
@@ -821,20 +819,14 @@ __global__ void __launch_bounds__(NT, 1)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     K::template prefetch<0>(c, g, p, src, pfb, 0);
     // Output rows without a wall, ghost or NEE role (warp-uniform) run the
-    // march with those tests compiled out, rows next to a bounce-back wall one
-    // with only the wall correction; the halo, ghost and NEE rows run the
-    // general one.
+    // march with those tests compiled out; the wall, halo, ghost and NEE rows
+    // run the general one.  (A third copy for the rows next to a bounce-back
+    // wall, with only the wall correction tested, paid off for 16-bit storage
+    // before the rows were permuted onto warps; after it, it made the BF16
+    // kernel spill 92 bytes instead of 24 and cost 1.2 %.)
     const bool plain = uni(c.warp >= 1 && c.warp <= YOUT && c.out_row && !c.zero_row && !c.nee_row &&
                            !((c.ybb || (!XFREE && yfs)) && (c.row_lo || c.row_hi)));
-    // (the wall march exists only in the 16-bit variants that can have
-    // bounce-back walls -- periodic x, no NEE walls, no sponge: BF16 channel
-    // 66.5 -> 68.1 GLUPS; with FP32 storage the third march made the kernel
-    // spill and measured 1.2 % slower, so FP32 keeps two)
-    constexpr bool WALLS = !XFREE && !NEEY && !SPONGE && sizeof(typename K::T) != 4;
-    const bool wall = WALLS && uni(c.warp >= 1 && c.warp <= YOUT && c.out_row && !c.zero_row && !c.nee_row &&
-                                   c.ybb && (c.row_lo || c.row_hi));
     if (plain) K::template march<ROLE_PLAIN>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
-    else if (WALLS && wall) K::template march<WALLS ? ROLE_WALL : ROLE_ANY>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
     else K::template march<ROLE_ANY>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
 }
 
