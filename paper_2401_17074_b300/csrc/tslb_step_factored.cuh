@@ -512,22 +512,13 @@ struct Kernel {
                 Q[3 + r] = pops3(Z[1][r].x, Z[0][r].y, Z[3][r].y);  // k1 = 1 (groups 1, 5, 7)
                 Q[6 + r] = pops2(Z[2][r].x, Z[3][r].x);             // k1 = 2 (groups 3, 6)
             }
-            if (ROLE == ROLE_ANY && role<HOIST>(c.zero_row)) {
-                // ghost row beyond a bounce-back wall: the entering deviation is zero
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int q = 0; q < YV; ++q) sv[q * NT + c.tid] = z4;
-                ss[c.tid] = 0.0f;
-                ss[NT + c.tid] = 0.0f;
-            } else {
-                // slot order 0 1 3 4 | 6 7 2 5: the (r = 0, r = 1) pair of each k1 is adjacent
-                sv[0 * NT + c.tid] = make_float4(Q[0].pp, Q[1].pp, Q[3].pp, Q[4].pp);
-                sv[1 * NT + c.tid] = make_float4(Q[6].pp, Q[7].pp, Q[2].pp, Q[5].pp);
-                sv[2 * NT + c.tid] = make_float4(Q[0].pm, Q[1].pm, Q[3].pm, Q[4].pm);
-                sv[3 * NT + c.tid] = make_float4(Q[6].pm, Q[7].pm, Q[2].pm, Q[5].pm);
-                ss[c.tid] = Q[8].pp;
-                ss[NT + c.tid] = Q[8].pm;
-            }
+            // slot order 0 1 3 4 | 6 7 2 5: the (r = 0, r = 1) pair of each k1 is adjacent
+            sv[0 * NT + c.tid] = make_float4(Q[0].pp, Q[1].pp, Q[3].pp, Q[4].pp);
+            sv[1 * NT + c.tid] = make_float4(Q[6].pp, Q[7].pp, Q[2].pp, Q[5].pp);
+            sv[2 * NT + c.tid] = make_float4(Q[0].pm, Q[1].pm, Q[3].pm, Q[4].pm);
+            sv[3 * NT + c.tid] = make_float4(Q[6].pm, Q[7].pm, Q[2].pm, Q[5].pm);
+            ss[c.tid] = Q[8].pp;
+            ss[NT + c.tid] = Q[8].pm;
             __syncwarp();
             mbar_arrive_if(&bars[c.warp * 2 + PAR], c.arrive);
             {
@@ -645,16 +636,6 @@ struct Kernel {
             ppOld[i] = P[i].pp;
             cNew[i] = P[i].c;
         }
-        if (ROLE == ROLE_ANY && role<HOIST>(c.zero_row) && (STEADY || (zs >= c.z0 && zs < c.z1))) {
-            // The ghost thread's column is clamped onto the wall-adjacent node,
-            // so its prefetch slots hold that node's moments at plane zs.
-            float m[NFIELDS];
-            NodeIO<Codec>::decode_smem_rawpi(v0, v1, v2, p, m);
-            float F0, F1, F2;
-            node_force<PAR>(c, g, p, pfb, idx, F0, F1, F2);
-            bounce_back_correction(m, F0, F1, F2, om_pi, c.y < 0 ? 1.0f : -1.0f,
-                                   corr + ((PAR * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
-        }
     }
 
     // The whole z march of one warp: planes 0 and 1 (ghost / wrap, no
@@ -679,6 +660,66 @@ struct Kernel {
         for (; j < c.np; j += 2) {
             plane_step<0, false, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j, ppA, cA, cB);
             if (j + 1 < c.np) plane_step<1, false, ROLE>(c, g, p, src, dst, ysm, pfb, corr, bars, dead, j + 1, ppB, cB, cA);
+        }
+    }
+
+    // The ghost row beyond a bounce-back wall: its exchange slots hold zeros
+    // (the deviation entering the wall row from it is zero), written once;
+    // each plane it keeps the exchange barriers' rhythm and hands the wall row
+    // the closed-form correction of the wall-adjacent node, onto which its
+    // column is clamped.
+    template <int PAR>
+    static __device__ __forceinline__ void ghost_step(const Ctx& c, const Geometry& g, const Physics& p,
+                                                      const T* __restrict__ src, char* pfb, float* corr,
+                                                      uint64_t* bars, bool& dead, int j) {
+        const int zs = c.z0 - 1 + j;
+        bool inflow_ghost;
+        int halo;
+        const int zl = plane_of<HALO>(zs, g, c.zper, inflow_ghost, halo);
+        const unsigned idx = c.col + c.plane * (unsigned)zl;
+        const int zfull = c.zper ? zl : zs + g.lo[2];
+        const float om_pi = (SPONGE && TSLB_IN_RANGE(zfull, g.nz + 2 * g.lo[2], p.err))
+                                ? __ldg(p.omega1_z + zfull) * p.s_pi
+                                : p.omega1_pi;
+        if (zs < c.z1) prefetch<PAR ^ 1>(c, g, p, src, pfb, j + 1);
+        else cp_async_commit();
+        cp_async_wait_prev();
+        if (zs >= c.z0 + 1) {
+            __syncwarp();
+            mbar_arrive_if(&bars[c.warp * 2 + PAR], c.arrive);
+            const unsigned par = (unsigned)((j - 2) >> 1) & 1u;
+            if (c.wait_lo) mbar_wait(&bars[(c.warp - 1) * 2 + PAR], par, p.err, dead);
+            if (c.wait_hi) mbar_wait(&bars[(c.warp + 1) * 2 + PAR], par, p.err, dead);
+        }
+        if (zs >= c.z0 && zs < c.z1) {
+            const char* pb = pfb + PAR * PF::BUF;
+            const T* v0 = reinterpret_cast<const T*>(pb + c.tid * PF::B01);
+            const T* v1 = reinterpret_cast<const T*>(pb + NT * PF::B01 + c.tid * PF::B01);
+            const T* v2 = reinterpret_cast<const T*>(pb + 2 * NT * PF::B01 + c.tid * PF::B2);
+            float m[NFIELDS];
+            NodeIO<Codec>::decode_smem_rawpi(v0, v1, v2, p, m);
+            float F0, F1, F2;
+            node_force<PAR>(c, g, p, pfb, idx, F0, F1, F2);
+            bounce_back_correction(m, F0, F1, F2, om_pi, c.y < 0 ? 1.0f : -1.0f,
+                                   corr + ((PAR * 2 + (c.y < 0 ? 0 : 1)) * 32 + c.lane) * NCORR);
+        }
+    }
+    static __device__ __forceinline__ void ghost_march(const Ctx& c, const Geometry& g, const Physics& p,
+                                                       const T* __restrict__ src, float* ysm, char* pfb, float* corr,
+                                                       uint64_t* bars, bool& dead) {
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            float4* sv = reinterpret_cast<float4*>(ysm + b * (YBUF / sizeof(float)));
+            float* ss = ysm + b * (YBUF / sizeof(float)) + 4 * YV * NT;
+#pragma unroll
+            for (int q = 0; q < YV; ++q) sv[q * NT + c.tid] = z4;
+            ss[c.tid] = 0.0f;
+            ss[NT + c.tid] = 0.0f;
+        }
+        for (int j = 0; j < c.np; j += 2) {
+            ghost_step<0>(c, g, p, src, pfb, corr, bars, dead, j);
+            if (j + 1 < c.np) ghost_step<1>(c, g, p, src, pfb, corr, bars, dead, j + 1);
         }
     }
 
@@ -826,7 +867,13 @@ __global__ void __launch_bounds__(NT, 1)
     // kernel spill 92 bytes instead of 24 and cost 1.2 %.)
     const bool plain = uni(c.warp >= 1 && c.warp <= YOUT && c.out_row && !c.zero_row && !c.nee_row &&
                            !((c.ybb || (!XFREE && yfs)) && (c.row_lo || c.row_hi)));
-    if (plain) K::template march<ROLE_PLAIN>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
+    // The ghost row beyond a bounce-back wall (warp-uniform) runs a march of
+    // its own: in the general one it computed the Hermite and z populations
+    // of its node every plane only to write zeros, and the tiles at a wall
+    // paced the launch (with the march of its own, and its branches taken out
+    // of the general march: BF16 +6 %, FP16 +2.5 %, FP32 +1.2 %).
+    if (uni(c.zero_row)) K::ghost_march(c, g, p, src, ysm, pfb, corr, bars, dead);
+    else if (plain) K::template march<ROLE_PLAIN>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
     else K::template march<ROLE_ANY>(c, g, p, src, dst, ysm, pfb, corr, bars, dead);
 }
 
