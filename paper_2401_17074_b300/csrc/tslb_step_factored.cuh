@@ -667,7 +667,11 @@ struct Kernel {
     // (the deviation entering the wall row from it is zero), written once;
     // each plane it keeps the exchange barriers' rhythm and hands the wall row
     // the closed-form correction of the wall-adjacent node, onto which its
-    // column is clamped.
+    // column is clamped.  The correction of plane zs, written at march step j
+    // into buffer PAR, is read by the wall row at step j + 1 after it has seen
+    // this row's arrival of step j + 1 (which follows the write, the warp
+    // synchronised); it is overwritten at step j + 2 only after this row has
+    // seen the wall row's arrival of step j + 2, which follows that read.
     template <int PAR>
     static __device__ __forceinline__ void ghost_step(const Ctx& c, const Geometry& g, const Physics& p,
                                                       const T* __restrict__ src, char* pfb, float* corr,
